@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the QMC American-option hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline leg of bench.py, never by the product library.  It shares no
+code with the CUDA path.  The arithmetic lives in ``amc_oracle.c`` (plain C,
+double precision, written step by step after the paper); this module only
+marshals numpy arrays into it and reads the raw Joe-Kuo data (primitive
+polynomials and initial direction numbers, Joe & Kuo 2008) from the data file
+that ships with scipy.
+
+Functions and the passages they follow:
+  shifts         digital shift per dimension, SplitMix64(seed) high words
+  directions     Sobol' direction numbers (Bratley-Fox recurrence)
+  sobol          32-bit Sobol' integers, Gray-code order (§III.D)
+  norm_icdf      inverse cumulative normal as the root of Phi(z)=u (§III.D)
+  bridge_schedule breadth-first Brownian-bridge bisection (ref. [13])
+  paths          steps 1-3: points -> normals -> bridge -> GBM (Eq. 9)
+  lsm            Longstaff-Schwartz sweep (ref. [12], §V backward induction)
+  paper_ub       the paper's exercise rule, Eqs. 10-11
+  european       Eqs. 6-8
+  bs             Black-Scholes, Eqs. 1-5
+  crr            Cox-Ross-Rubinstein tree (Bermudan or American)
+  pathwise_greeks frozen-boundary pathwise delta and vega
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+PUT, CALL = 0, 1
+RULE_LSM, RULE_PAPER_UB, RULE_EUROPEAN = 0, 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(_build.build())
+        lib.orc_splitmix64_next.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        lib.orc_splitmix64_next.restype = ctypes.c_uint64
+        lib.orc_digital_shifts.argtypes = [ctypes.c_uint64, ctypes.c_int, _u32p]
+        lib.orc_sobol_directions.argtypes = [ctypes.c_int, _i64p, _i64p, ctypes.c_int, _u32p]
+        lib.orc_sobol_direct.argtypes = [_u32p, ctypes.c_int, ctypes.c_uint64]
+        lib.orc_sobol_direct.restype = ctypes.c_uint32
+        lib.orc_sobol_block.argtypes = [_u32p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, _u32p]
+        lib.orc_norm_cdf.argtypes = [ctypes.c_double]
+        lib.orc_norm_cdf.restype = ctypes.c_double
+        lib.orc_norm_icdf.argtypes = [ctypes.c_double]
+        lib.orc_norm_icdf.restype = ctypes.c_double
+        lib.orc_uniform.argtypes = [ctypes.c_uint32]
+        lib.orc_uniform.restype = ctypes.c_double
+        lib.orc_bridge_schedule.argtypes = [ctypes.c_int, _ip, _ip, _ip]
+        lib.orc_paths.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, _u32p, _u32p, _dp, _dp]
+        lib.orc_bs.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5
+        lib.orc_bs.restype = ctypes.c_double
+        lib.orc_solve_normal.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+        lib.orc_lsm.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _i32p, _dp, _i64p]
+        lib.orc_paper_ub.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
+        lib.orc_european.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
+        lib.orc_pathwise_greeks.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 5 +
+                                            [ctypes.c_int, ctypes.c_int64, _dp, _dp, _i32p, _dp])
+        lib.orc_crr.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int] * 3
+        lib.orc_crr.restype = ctypes.c_double
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+# ----------------------------------------------------------------------------
+def joe_kuo_raw(m):
+    """Raw Joe-Kuo data for dimensions 0..m-1: (poly int64[m], vinit int64[m,18])."""
+    import scipy.stats
+    path = os.path.join(os.path.dirname(scipy.stats.__file__), "_sobol_direction_numbers.npz")
+    with np.load(path) as d:
+        poly = np.ascontiguousarray(d["poly"][:m], dtype=np.int64)
+        vinit = np.ascontiguousarray(d["vinit"][:m], dtype=np.int64)
+    if poly.shape[0] < m:
+        raise ValueError("Joe-Kuo data holds %d dimensions, %d asked" % (poly.shape[0], m))
+    return poly, vinit
+
+
+def splitmix64(seed, n):
+    st = ctypes.c_uint64(seed)
+    return [_lib().orc_splitmix64_next(ctypes.byref(st)) for _ in range(n)]
+
+
+def shifts(seed, m):
+    out = np.zeros(m, dtype=np.uint32)
+    _lib().orc_digital_shifts(ctypes.c_uint64(seed), m, _ptr(out, _u32p))
+    return out
+
+
+def directions(m):
+    poly, vinit = joe_kuo_raw(m)
+    V = np.zeros((m, 32), dtype=np.uint32)
+    rc = _lib().orc_sobol_directions(m, _ptr(poly, _i64p), _ptr(vinit, _i64p), vinit.shape[1], _ptr(V, _u32p))
+    if rc != 0:
+        raise ValueError("direction-number expansion failed (%d)" % rc)
+    return V
+
+
+def sobol(n, m, i0=0, seed=None, V=None):
+    """Unshifted (seed None) or shifted Sobol' integers, shape (m, n), points i0..i0+n-1."""
+    if V is None:
+        V = directions(m)
+    X = np.zeros((m, n), dtype=np.uint32)
+    _lib().orc_sobol_block(_ptr(V, _u32p), m, ctypes.c_uint64(i0), n, _ptr(X, _u32p))
+    if seed is not None:
+        X ^= shifts(seed, m)[:, None]
+    return X
+
+
+def sobol_direct(V, d, i):
+    return _lib().orc_sobol_direct(_ptr(V, _u32p), d, ctypes.c_uint64(i))
+
+
+def norm_icdf(u):
+    f = _lib().orc_norm_icdf
+    return np.array([f(float(x)) for x in np.ravel(u)]).reshape(np.shape(u))
+
+
+def norm_cdf(x):
+    f = _lib().orc_norm_cdf
+    return np.array([f(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def uniform(x):
+    f = _lib().orc_uniform
+    return np.array([f(int(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def bridge_schedule(m):
+    date = np.zeros(m, dtype=np.intc)
+    left = np.zeros(m, dtype=np.intc)
+    right = np.zeros(m, dtype=np.intc)
+    if _lib().orc_bridge_schedule(m, _ptr(date, _ip), _ptr(left, _ip), _ptr(right, _ip)) != 0:
+        raise ValueError("bridge schedule failed")
+    return date, left, right
+
+
+def paths(S0, r, sigma, T, m, N, seed, with_W=False):
+    """Steps 1-3: S of shape (m, N), S[j-1, i] = S_i(t_j); optionally W too."""
+    V = directions(m)
+    sh = shifts(seed, m)
+    S = np.empty((m, N), dtype=np.float64)
+    W = np.empty((m, N), dtype=np.float64) if with_W else None
+    rc = _lib().orc_paths(S0, r, sigma, T, m, N, _ptr(V, _u32p), _ptr(sh, _u32p), _ptr(S, _dp), _ptr(W, _dp))
+    if rc != 0:
+        raise MemoryError("oracle path generation failed (%d)" % rc)
+    return (S, W) if with_W else S
+
+
+def bs(type_, S, K, r, sigma, T):
+    return _lib().orc_bs(type_, S, K, r, sigma, T)
+
+
+def solve_normal(G, b):
+    p = len(b)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    beta = np.zeros(p)
+    rc = _lib().orc_solve_normal(p, _ptr(G, _dp), _ptr(b, _dp), _ptr(beta, _dp))
+    return (None if rc else beta)
+
+
+def lsm(S, type_, K, r, T, p, details=False):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    m, N = S.shape
+    out = np.zeros(3)
+    beta = np.zeros((m, p)) if details else None
+    tau = np.zeros(N, dtype=np.int32) if details else None
+    cf = np.zeros(N) if details else None
+    nitm = np.zeros(m, dtype=np.int64) if details else None
+    rc = _lib().orc_lsm(type_, K, r, T, m, N, p, _ptr(S, _dp), _ptr(out, _dp), _ptr(beta, _dp),
+                        _ptr(tau, _i32p), _ptr(cf, _dp), _ptr(nitm, _i64p))
+    if rc != 0:
+        raise ValueError("oracle lsm failed")
+    res = {"price": out[0], "std_err": out[1], "degenerate_dates": int(out[2])}
+    if details:
+        res.update(beta=beta, tau=tau, cf=cf, n_itm=nitm)
+    return res
+
+
+def paper_ub(S, type_, S0, K, r, sigma, T):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    m, N = S.shape
+    out = np.zeros(3)
+    _lib().orc_paper_ub(type_, S0, K, r, sigma, T, m, N, _ptr(S, _dp), _ptr(out, _dp))
+    return {"price": out[0], "std_err": out[1], "degenerate_dates": 0}
+
+
+def paper_ub_m1(type_, S0, K, r, sigma, T):
+    """m = 1 needs no paths: max(h(S0), BS(S0, K, T))."""
+    out = np.zeros(3)
+    S = np.zeros(1)
+    _lib().orc_paper_ub(type_, S0, K, r, sigma, T, 1, 1, _ptr(S, _dp), _ptr(out, _dp))
+    return out[0]
+
+
+def european(S, type_, K, r, T):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    m, N = S.shape
+    out = np.zeros(3)
+    _lib().orc_european(type_, K, r, T, m, N, _ptr(S, _dp), _ptr(out, _dp))
+    return {"price": out[0], "std_err": out[1], "degenerate_dates": 0}
+
+
+def pathwise_greeks(S, W, tau, type_, S0, K, r, sigma, T):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.int32)
+    m, N = S.shape
+    out = np.zeros(3)
+    rc = _lib().orc_pathwise_greeks(type_, S0, K, r, sigma, T, m, N, _ptr(S, _dp), _ptr(W, _dp),
+                                    _ptr(tau, _i32p), _ptr(out, _dp))
+    if rc != 0:
+        raise ValueError("bad tau")
+    return {"price": out[0], "delta": out[1], "vega": out[2]}
+
+
+def crr(type_, S0, K, r, sigma, T, n, m=1, bermudan=False):
+    return _lib().orc_crr(type_, S0, K, r, sigma, T, n, m, 1 if bermudan else 0)
+
+
+# ----------------------------------------------------------------------------
+def price(S0, K, r, sigma, T, n_steps, n_paths, basis=3, type=PUT, seed=0, rule=RULE_LSM, details=False):
+    """Full oracle pricing of one option on its own Sobol' points."""
+    S = paths(S0, r, sigma, T, n_steps, n_paths, seed)
+    if rule == RULE_LSM:
+        return lsm(S, type, K, r, T, basis, details=details)
+    if rule == RULE_PAPER_UB:
+        return paper_ub(S, type, S0, K, r, sigma, T)
+    if rule == RULE_EUROPEAN:
+        return european(S, type, K, r, T)
+    raise ValueError("unknown rule")
+
+
+def greeks(S0, K, r, sigma, T, n_steps, n_paths, basis=3, type=PUT, seed=0, rule=RULE_LSM):
+    """Frozen-boundary pathwise price, delta and vega on the oracle's paths."""
+    S, W = paths(S0, r, sigma, T, n_steps, n_paths, seed, with_W=True)
+    if rule == RULE_LSM:
+        tau = lsm(S, type, K, r, T, basis, details=True)["tau"]
+    elif rule == RULE_EUROPEAN:
+        tau = np.full(n_paths, n_steps, dtype=np.int32)
+    else:
+        raise ValueError("greeks are defined for the LSM and European rules")
+    return pathwise_greeks(S, W, tau, type, S0, K, r, sigma, T)
+
+
+def bridge_matrix(m, T):
+    """W = A z for one path; A[j-1, k] = weight of coordinate k on W(t_j)."""
+    A = np.zeros((m, m))
+    lib = _lib()
+    lib.orc_bridge_matrix.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+    if lib.orc_bridge_matrix(m, T, _ptr(A, _dp)) != 0:
+        raise ValueError("bridge matrix failed")
+    return A

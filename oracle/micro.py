@@ -1,0 +1,41 @@
+"""Second, independent LSM oracle for tiny inputs (numpy; test infrastructure).
+
+Longstaff & Schwartz (ref. [12] of the paper) written a second way: the
+regression at each date is an ordinary least-squares fit by
+``numpy.linalg.lstsq`` (SVD) instead of equilibrated normal equations, and the
+loop keeps whole-array state.  Used only on a handful of paths and dates so
+that its per-date coefficients, cash flows and stopping dates can be compared
+with the C oracle entry by entry.
+"""
+import numpy as np
+
+
+def lsm_micro(S, type_, K, r, T, p):
+    """S: (m, N) date-major paths.  Returns dict(price, beta (m,p), tau, cf, degenerate)."""
+    S = np.asarray(S, dtype=np.float64)
+    m, N = S.shape
+    dt = T / m
+    disc = np.exp(-r * dt)
+    pay = (lambda s: np.maximum(s - K, 0.0)) if type_ == 1 else (lambda s: np.maximum(K - s, 0.0))
+    cf = pay(S[m - 1]).copy()
+    tau = np.full(N, m, dtype=np.int32)
+    beta = np.zeros((m, p))
+    degenerate = 0
+    for j in range(m - 1, 0, -1):
+        cf = cf * disc
+        h = pay(S[j - 1])
+        itm = np.nonzero(h > 0)[0]
+        if itm.size < p:
+            degenerate += 1
+            continue
+        x = S[j - 1, itm] / K
+        X = np.vander(x, p, increasing=True)
+        if np.linalg.matrix_rank(X) < p:
+            degenerate += 1
+            continue
+        b, *_ = np.linalg.lstsq(X, cf[itm], rcond=None)
+        beta[j - 1] = b
+        ex = itm[h[itm] > X @ b]
+        cf[ex] = h[ex]
+        tau[ex] = j
+    return {"price": disc * cf.mean(), "beta": beta, "tau": tau, "cf": cf, "degenerate_dates": degenerate}

@@ -1,0 +1,317 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test ties one oracle function to an independent source: scipy's own
+Sobol' and inverse-normal routines, printed worked examples (tests/golden/),
+closed forms, invariants of the method, or a second implementation written a
+different way (oracle/micro.py).  A dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of these.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.micro import lsm_micro
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- SplitMix64
+def test_splitmix64_published_outputs():
+    g = _golden("splitmix64_seed0.json")
+    assert oracle.splitmix64(g["seed"], 3) == [int(h, 16) for h in g["outputs_hex"]]
+
+
+def test_digital_shift_is_high_word():
+    outs = oracle.splitmix64(12345, 7)
+    assert list(oracle.shifts(12345, 7)) == [o >> 32 for o in outs]
+
+
+# ---------------------------------------------------------------- Sobol'
+@pytest.mark.parametrize("m", [1, 2, 50, 252, 365, 512])
+def test_sobol_bit_exact_vs_scipy(m):
+    from scipy.stats import qmc
+    n = 1024
+    eng = qmc.Sobol(d=m, scramble=False, bits=32)
+    ref = np.round(eng.random(n) * 2.0 ** 32).astype(np.uint64).T
+    X = oracle.sobol(n, m).astype(np.uint64)
+    np.testing.assert_array_equal(X, ref)
+
+
+def test_sobol_gray_recurrence_equals_direct_formula():
+    m = 40
+    V = oracle.directions(m)
+    rng = np.random.default_rng(0)
+    for i0 in [0, 1, 4095, 2 ** 20 - 3, 3 * 2 ** 27 + 11]:
+        X = oracle.sobol(9, m, i0=i0, V=V)
+        for t in range(9):
+            for d in rng.choice(m, 5, replace=False):
+                assert X[d, t] == oracle.sobol_direct(V, int(d), i0 + t)
+
+
+def test_sobol_first_dims_are_textbook():
+    V = oracle.directions(3)
+    # dim 0: van der Corput; dim 1 (x+1, m1=1): m_k = 1, 3, 5, 15, ... (v_k = m_k/2^k)
+    assert [int(v) for v in V[0, :4]] == [1 << 31, 1 << 30, 1 << 29, 1 << 28]
+    assert [int(V[1, k]) >> (31 - k) for k in range(5)] == [1, 3, 5, 15, 17]
+
+
+def test_shifted_points_are_xor():
+    X0 = oracle.sobol(64, 10)
+    X1 = oracle.sobol(64, 10, seed=7)
+    np.testing.assert_array_equal(X1, X0 ^ oracle.shifts(7, 10)[:, None])
+
+
+# ---------------------------------------------------------------- inverse normal
+def test_norm_icdf_vs_scipy_ndtri():
+    from scipy.special import ndtri
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.integers(0, 2 ** 32, 4000, dtype=np.uint64),
+                         np.array([0, 1, 2, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 2, 2 ** 32 - 1], dtype=np.uint64)])
+    u = oracle.uniform(xs)
+    assert np.all((u > 0) & (u < 1))
+    z = oracle.norm_icdf(u)
+    ref = ndtri(u)
+    np.testing.assert_allclose(z, ref, rtol=2e-14, atol=2e-15)
+
+
+def test_norm_cdf_vs_scipy():
+    from scipy.special import ndtr
+    x = np.linspace(-9, 9, 1001)
+    np.testing.assert_allclose(oracle.norm_cdf(x), ndtr(x), rtol=1e-14, atol=1e-300)
+
+
+# ---------------------------------------------------------------- Brownian bridge
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 7, 12, 50, 64, 100, 252, 365])
+def test_bridge_covariance_is_min(m):
+    T = 1.7
+    A = oracle.bridge_matrix(m, T)
+    t = np.arange(1, m + 1) * (T / m)
+    np.testing.assert_allclose(A @ A.T, np.minimum.outer(t, t), atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 50, 252, 365])
+def test_bridge_schedule_visits_every_date_once(m):
+    date, left, right = oracle.bridge_schedule(m)
+    assert sorted(date.tolist()) == list(range(1, m + 1))
+    assert date[0] == m
+    seen = {0, m}
+    for k in range(1, m):
+        assert left[k] in seen and right[k] in seen and left[k] < date[k] < right[k]
+        seen.add(int(date[k]))
+
+
+def test_bridge_power_of_two_is_textbook_bisection():
+    m = 16
+    date, _, _ = oracle.bridge_schedule(m)
+    expect = [16, 8, 4, 12, 2, 6, 10, 14, 1, 3, 5, 7, 9, 11, 13, 15]
+    assert date.tolist() == expect
+
+
+# ---------------------------------------------------------------- GBM
+def test_gbm_log_space_equals_iterated_eq9():
+    S0, r, sigma, T, m = 100.0, 0.05, 0.3, 1.0, 12
+    S, W = oracle.paths(S0, r, sigma, T, m, 64, seed=3, with_W=True)
+    dt = T / m
+    prev, Wprev = np.full(64, S0), np.zeros(64)
+    for j in range(m):
+        prev = prev * np.exp((r - 0.5 * sigma ** 2) * dt + sigma * (W[j] - Wprev))
+        Wprev = W[j]
+        np.testing.assert_allclose(S[j], prev, rtol=1e-13)
+
+
+def test_gbm_martingale_each_date():
+    S0, r, sigma, T, m, N = 100.0, 0.05, 0.3, 1.0, 16, 2 ** 14
+    S = oracle.paths(S0, r, sigma, T, m, N, seed=11)
+    t = np.arange(1, m + 1) * (T / m)
+    disc_mean = (np.exp(-r * t)[:, None] * S).mean(axis=1)
+    np.testing.assert_allclose(disc_mean, S0, rtol=2e-3)
+
+
+# ---------------------------------------------------------------- Black-Scholes
+def test_bs_textbook_example():
+    g = _golden("bs_textbook_example.json")
+    c = oracle.bs(oracle.CALL, g["S0"], g["K"], g["r"], g["sigma"], g["T"])
+    p = oracle.bs(oracle.PUT, g["S0"], g["K"], g["r"], g["sigma"], g["T"])
+    assert abs(c - g["call"]) < g["tol"] and abs(p - g["put"]) < g["tol"]
+
+
+@pytest.mark.parametrize("S0,K,r,sigma,T", [(36, 40, .06, .2, 1), (100, 100, .05, .3, 1), (90, 110, 0.0, .5, 2)])
+def test_bs_put_call_parity(S0, K, r, sigma, T):
+    c = oracle.bs(oracle.CALL, S0, K, r, sigma, T)
+    p = oracle.bs(oracle.PUT, S0, K, r, sigma, T)
+    assert abs((c - p) - (S0 - K * math.exp(-r * T))) < 1e-12
+
+
+def test_bs_equals_converged_european_tree():
+    for tp in (oracle.PUT, oracle.CALL):
+        bs = oracle.bs(tp, 36, 40, .06, .2, 1.0)
+        tree = oracle.crr(tp, 36, 40, .06, .2, 1.0, 20000, 1, bermudan=True)
+        assert abs(bs - tree) < 2e-4
+
+
+# ---------------------------------------------------------------- CRR tree
+def test_crr_american_call_equals_european_call():
+    c_am = oracle.crr(oracle.CALL, 100, 100, .05, .3, 1.0, 4000)
+    c_eu = oracle.crr(oracle.CALL, 100, 100, .05, .3, 1.0, 4000, 1, bermudan=True)
+    assert abs(c_am - c_eu) < 1e-10
+
+
+def test_crr_ordering_european_bermudan_american():
+    eu = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000, 1, bermudan=True)
+    be = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000, 50, bermudan=True)
+    am = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000)
+    assert eu < be < am
+    assert be > 40 - 36 - 1e-12
+
+
+# ---------------------------------------------------------------- normal equations
+def test_solve_normal_matches_lstsq_and_flags_singular():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.3, 1.0, 200)
+    y = rng.normal(size=200)
+    X = np.vander(x, 4, increasing=True)
+    beta = oracle.solve_normal(X.T @ X, X.T @ y)
+    ref, *_ = np.linalg.lstsq(X, y, rcond=None)
+    np.testing.assert_allclose(beta, ref, rtol=1e-7, atol=1e-9)
+    Xs = np.vander(np.full(10, 0.7), 3, increasing=True)       # rank 1
+    assert oracle.solve_normal(Xs.T @ Xs, Xs.T @ np.ones(10)) is None
+
+
+# ---------------------------------------------------------------- LSM
+def test_lsm_longstaff_schwartz_worked_example():
+    g = _golden("ls2001_example.json")
+    S = np.array(g["paths_t1_t2_t3"]).T          # (m=3, N=8) date-major
+    res = oracle.lsm(S, oracle.PUT, g["K"], g["r"], g["T"], 3, details=True)
+    assert abs(res["price"] - g["value"]) < g["value_tol"]
+    K = g["K"]
+    scale = np.array([1.0, K, K * K])             # basis in x = S/K -> basis in S
+    np.testing.assert_allclose(res["beta"][1] / scale, g["regression_t2_in_S"], atol=g["coef_tol"])
+    np.testing.assert_allclose(res["beta"][0] / scale, g["regression_t1_in_S"], atol=g["coef_tol"])
+    # stopping dates: 0 in the fixture means never exercised (our tau = m with zero payoff)
+    h = np.maximum(K - S, 0.0)
+    stop = [0 if h[t - 1, i] == 0 else t for i, t in enumerate(res["tau"])]
+    assert stop == g["stopping_date_per_path"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lsm_matches_independent_micro_oracle(seed):
+    rng = np.random.default_rng(100 + seed)
+    m, N, K, r, T = 3, 8, 1.0, 0.05, 1.0
+    S = np.exp(rng.normal(0, 0.15, (m, N)).cumsum(axis=0)) * 0.97
+    for tp in (oracle.PUT, oracle.CALL):
+        a = oracle.lsm(S, tp, K, r, T, 2 if seed % 2 else 3, details=True)
+        b = lsm_micro(S, tp, K, r, T, 2 if seed % 2 else 3)
+        assert abs(a["price"] - b["price"]) < 1e-12
+        np.testing.assert_array_equal(a["tau"], b["tau"])
+        np.testing.assert_allclose(a["beta"], b["beta"], rtol=1e-6, atol=1e-9)  # normal equations square cond(X)
+        assert a["degenerate_dates"] == b["degenerate_dates"]
+
+
+def test_lsm_micro_oracle_on_sobol_paths():
+    S = oracle.paths(36.0, .06, .2, 1.0, 6, 64, seed=1)
+    a = oracle.lsm(S, oracle.PUT, 40.0, .06, 1.0, 3, details=True)
+    b = lsm_micro(S, oracle.PUT, 40.0, .06, 1.0, 3)
+    assert abs(a["price"] - b["price"]) < 1e-12
+    np.testing.assert_array_equal(a["tau"], b["tau"])
+
+
+def _rqmc(fn, R=16, base=1000):
+    vals = np.array([fn(base + k) for k in range(R)])
+    return vals.mean(), vals.std(ddof=1) / math.sqrt(R)
+
+
+def test_european_limit_vs_black_scholes():
+    for tp in (oracle.PUT, oracle.CALL):
+        mean, se = _rqmc(lambda s: oracle.price(36, 40, .06, .2, 1.0, 16, 2 ** 12, type=tp, seed=s,
+                                                rule=oracle.RULE_EUROPEAN)["price"])
+        assert abs(mean - oracle.bs(tp, 36, 40, .06, .2, 1.0)) < 4 * se + 1e-4
+
+
+def test_american_call_without_dividends_equals_european():
+    mean, se = _rqmc(lambda s: oracle.price(100, 100, .05, .3, 1.0, 20, 2 ** 12, basis=3, type=oracle.CALL,
+                                            seed=s)["price"])
+    bs = oracle.bs(oracle.CALL, 100, 100, .05, .3, 1.0)
+    assert abs(mean - bs) < 4 * se + 0.005 * bs
+
+
+def test_american_at_least_european_and_intrinsic():
+    for (S0, K) in [(36, 40), (44, 40), (30, 40)]:
+        res = oracle.price(S0, K, .06, .2, 1.0, 50, 2 ** 13, basis=3, type=oracle.PUT, seed=1)
+        eu = oracle.bs(oracle.PUT, S0, K, .06, .2, 1.0)
+        assert res["price"] >= eu - 3 * res["std_err"]
+        # t = 0 is not an exercise date, so the intrinsic bound is that of
+        # exercising at t_1: E[e^{-r t_1}(K - S_1)^+] >= K e^{-r t_1} - S0 (Jensen)
+        assert res["price"] >= max(K * math.exp(-.06 / 50) - S0, 0) - 3 * res["std_err"]
+
+
+def test_lsm_vs_bermudan_crr_tree():
+    m = 50
+    mean, se = _rqmc(lambda s: oracle.price(36, 40, .06, .2, 1.0, m, 2 ** 13, basis=3, seed=s)["price"], R=8)
+    tree = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000, m, bermudan=True)
+    assert abs(mean - tree) < 4 * se + 0.005 * tree
+
+
+# ---------------------------------------------------------------- paper rule
+def test_paper_rule_one_date_is_max_of_intrinsic_and_bs():
+    for tp, S0 in [(oracle.PUT, 36.0), (oracle.CALL, 44.0), (oracle.PUT, 30.0)]:
+        v = oracle.paper_ub_m1(tp, S0, 40.0, .06, .2, 1.0)
+        assert v == max(max((40 - S0) if tp == oracle.PUT else (S0 - 40), 0.0), oracle.bs(tp, S0, 40, .06, .2, 1.0))
+
+
+def test_paper_rule_is_discounted_pathwise_maximum():
+    S0, K, r, sigma, T, m = 36.0, 40.0, .06, .2, 1.0, 7
+    S = oracle.paths(S0, r, sigma, T, m, 512, seed=4)
+    got = oracle.paper_ub(S, oracle.PUT, S0, K, r, sigma, T)["price"]
+    dt = T / m
+    full = np.vstack([np.full((1, 512), S0), S])           # dates 0..m
+    h = np.maximum(K - full, 0.0)
+    last = np.maximum(h[m - 1], [oracle.bs(oracle.PUT, s, K, r, sigma, dt) for s in full[m - 1]])
+    terms = [np.exp(-r * j * dt) * h[j] for j in range(m - 1)] + [np.exp(-r * (m - 1) * dt) * last]
+    assert abs(got - np.max(terms, axis=0).mean()) < 1e-12
+
+
+def test_paper_rule_above_lsm_above_european():
+    for tp, S0 in [(oracle.PUT, 36.0), (oracle.CALL, 44.0)]:
+        S = oracle.paths(S0, .06, .2, 1.0, 25, 2 ** 12, seed=9)
+        ub = oracle.paper_ub(S, tp, S0, 40.0, .06, .2, 1.0)["price"]
+        ls = oracle.lsm(S, tp, 40.0, .06, 1.0, 3)["price"]
+        eu = oracle.european(S, tp, 40.0, .06, 1.0)["price"]
+        assert ub >= ls >= eu - 0.01
+
+
+# ---------------------------------------------------------------- Greeks
+def test_european_pathwise_greeks_vs_closed_form():
+    S0, K, r, sigma, T = 100.0, 100.0, .05, .3, 1.0
+    d1 = (math.log(S0 / K) + (r + .5 * sigma ** 2) * T) / (sigma * math.sqrt(T))
+    g = [oracle.greeks(S0, K, r, sigma, T, 8, 2 ** 12, type=oracle.PUT, seed=s, rule=oracle.RULE_EUROPEAN)
+         for s in range(8)]
+    delta = np.mean([x["delta"] for x in g])
+    vega = np.mean([x["vega"] for x in g])
+    Nd1 = 0.5 * math.erfc(-d1 / math.sqrt(2))
+    assert abs(delta - (Nd1 - 1)) < 2e-3
+    assert abs(vega - S0 * math.exp(-.5 * d1 * d1) / math.sqrt(2 * math.pi) * math.sqrt(T)) < 0.2
+
+
+def test_lsm_pathwise_greeks_vs_central_differences():
+    # enough paths that exercise-boundary crossings under the bump average out
+    S0, K, r, sigma, T, m, N = 36.0, 40.0, .06, .2, 1.0, 10, 2 ** 16
+    g = oracle.greeks(S0, K, r, sigma, T, m, N, basis=3, seed=5)
+    bS, bv = 1e-3 * S0, 1e-3 * sigma
+    up = oracle.price(S0 + bS, K, r, sigma, T, m, N, basis=3, seed=5)["price"]
+    dn = oracle.price(S0 - bS, K, r, sigma, T, m, N, basis=3, seed=5)["price"]
+    vu = oracle.price(S0, K, r, sigma + bv, T, m, N, basis=3, seed=5)["price"]
+    vd = oracle.price(S0, K, r, sigma - bv, T, m, N, basis=3, seed=5)["price"]
+    fd_delta, fd_vega = (up - dn) / (2 * bS), (vu - vd) / (2 * bv)
+    assert abs(g["delta"] - fd_delta) < 0.02 * abs(fd_delta) + 5e-3
+    assert abs(g["vega"] - fd_vega) < 0.05 * abs(fd_vega) + 0.2
+    base = oracle.price(S0, K, r, sigma, T, m, N, basis=3, seed=5)["price"]
+    assert abs(g["price"] - base) < 1e-12
