@@ -1,0 +1,308 @@
+"""Benchmark of the QMC American-option hot path on GB300.
+
+Workload (N=1): one American put, S0=100, K=100, r=0.05, sigma=0.3, T=1,
+252 exercise dates, 2^20 Sobol' paths, LSM basis {1,x,x^2,x^3}, shift seed 2
+(synthetic; the paper has no dataset).  One step = one full pricing: path
+generation (Sobol' -> inverse normal -> bridge -> GBM store) and the LSM
+backward sweep with its final sums, in the mixed precision (FP32 paths and
+compensated FP32 sums, FP64 solve and price).  Metric: path-steps/s =
+n_paths * n_steps / time per step.  The path array (1.06 GB) is larger than
+L2, so every step streams it from HBM.
+
+Keys beyond the base contract: fp64 (the same step in all-FP64 on the GPU),
+err_vs_oracle (|price - FP64 oracle price| on identical points, in units of
+K), roofline (dominant kernel) and roofline_sweep, cpu_baseline (the oracle
+on a bounded sample, host cores), clocks.
+
+Multi-GPU (torchrun, N>1): independent replicas, one option per rank (shift
+seed 2 + rank), no collective on the data path; value sums all ranks.
+
+--impl reference: the FP64 CPU oracle as it stands, on the host cores, on a
+bounded sample of the same workload per step (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "path-steps/s"
+CONFIG_NAME = "american_put_lsm_2^20paths_252dates_p4"
+
+
+def _config(opt, extra=None):
+    c = {"workload": CONFIG_NAME, "n_paths": opt.n_paths, "n_steps": opt.n_steps, "basis": opt.basis,
+         "type": "put", "S0": opt.S0, "K": opt.K, "r": opt.r, "sigma": opt.sigma, "T": opt.T,
+         "l2": "path array 1.06 GB > 129 MB L2 (streamed every step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "amc_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(opt, n_sample=2 ** 16):
+    """The FP64 oracle as it stands on a bounded sample (first n_sample paths)."""
+    import oracle
+    t = time.perf_counter()
+    S = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, n_sample, opt.seed)
+    oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
+    dt = time.perf_counter() - t
+    return {"value": n_sample * opt.n_steps / dt, "unit": METRIC, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "first %d of %d paths, all %d dates, paths + LSM sweep, %.1f s" % (
+                n_sample, opt.n_paths, opt.n_steps, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    opt = workloads.single_large()
+    n_sample = 2 ** 14
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        S = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, n_sample, opt.seed)
+        oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    per = sum(times) / len(times)
+    value = n_sample * opt.n_steps / per
+    sample = "first %d of %d paths, all %d dates per step (paths + LSM sweep)" % (n_sample, opt.n_paths,
+                                                                                   opt.n_steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(opt, {"sample_paths": n_sample}),
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(), "sample": sample, "value": value,
+                             "unit": METRIC},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_amc(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+        __graft_entry__.build()
+    import paper_1205_0106_gb300 as amc
+
+    opt = workloads.single_large()
+    if ws > 1:
+        opt = workloads.Option(**{**opt.as_dict(), "seed": opt.seed + rank})
+    ctx = amc.Context(local, arena_bytes=4 << 30)
+    stream = torch.cuda.Stream()
+    ld = amc.amc_path_ld(opt.n_paths)
+    units = opt.n_paths * opt.n_steps
+
+    def time_steps(prec, steps, warmup, split=False):
+        dt = torch.float64 if prec == amc.AMC_FP64 else torch.float32
+        S = torch.empty((opt.n_steps, ld), dtype=dt, device="cuda")
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                amc.amc_price_device(ctx, opt, prec, S, res, stream=stream)
+            stream.synchronize()
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps + 1 if split else 2)]
+            if split:
+                ev[0].record(stream)
+                for k in range(steps):
+                    amc.amc_generate_paths(ctx, opt, prec, S, stream=stream)
+                    ev[2 * k + 1].record(stream)
+                    amc.amc_sweep(ctx, opt, prec, S, res, stream=stream)
+                    ev[2 * k + 2].record(stream)
+            else:
+                ev[0].record(stream)
+                for _ in range(steps):
+                    amc.amc_price_device(ctx, opt, prec, S, res, stream=stream)
+                ev[1].record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+        if split:
+            gen = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
+            swp = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(steps)]
+            total = ev[0].elapsed_time(ev[2 * steps])
+            return total, sum(gen) / steps, sum(swp) / steps, res
+        return ev[0].elapsed_time(ev[1]), None, None, res
+
+    clocks = Clocks(torch.cuda.current_device())
+    # headline: mixed precision, device-resident
+    clocks.start()
+    t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
+    ck = clocks.stop()
+    t_tensor = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    t_ms = float(t_tensor.item())
+    ms_per_step = t_ms / args.steps
+    value = units * ws / (ms_per_step * 1e-3)
+    price = amc.res_to_dict(res.cpu().numpy())
+
+    # per-kernel times (same steps, generate and sweep timed apart)
+    _, gen_ms, sweep_ms, _ = time_steps(amc.AMC_MIXED, max(3, args.steps // 2), 2, split=True)
+    # FP64 GPU baseline on identical points
+    f_ms, _, _, fres = time_steps(amc.AMC_FP64, max(3, args.steps // 4), 2)
+    fp64_ms = f_ms / max(3, args.steps // 4)
+    fp64_price = amc.res_to_dict(fres.cpu().numpy())["price"]
+
+    # end to end through the host API: option in, price out (host buffers)
+    for _ in range(2):
+        amc.amc_price_american(ctx, opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, opt.basis,
+                               opt.type, opt.seed, opt.rule, amc.AMC_MIXED)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        amc.amc_price_american(ctx, opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, opt.basis,
+                               opt.type, opt.seed, opt.rule, amc.AMC_MIXED)
+    e2e_s = time.perf_counter() - t0
+    e_tensor = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e_tensor, op=dist.ReduceOp.MAX)
+    e2e_value = units * ws * args.steps / float(e_tensor.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = _peaks()
+    bytes_sweep = 4.0 * units                       # S read once: 4 B per path-step
+    bytes_gen = 4.0 * units                         # S written once
+    sweep_gbs = bytes_sweep / (sweep_ms * 1e-3) / 1e9
+    gen_gbs = bytes_gen / (gen_ms * 1e-3) / 1e9
+    rl_sweep = {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s", "frac": sweep_gbs / hbm,
+                "traffic": None, "kernel": "sweep_lsm_kernel", "ms": sweep_ms, "peak_kind": peak_kind}
+    rl_gen = {"bound": "hbm", "achieved": gen_gbs, "peak": hbm, "unit": "GB/s", "frac": gen_gbs / hbm,
+              "traffic": None, "kernel": "pathgen_kernel", "ms": gen_ms, "peak_kind": peak_kind}
+    dominant = rl_gen if gen_ms >= sweep_ms else rl_sweep
+    err = None
+    if not args.no_oracle_check:
+        import oracle
+        ref = oracle.price(opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, basis=opt.basis,
+                           type=opt.type, seed=opt.seed)
+        err = abs(price["price"] - ref["price"]) / opt.K
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": _config(opt, {"parallelism": "replicas" if ws > 1 else "single"}),
+            "price": price["price"], "std_err": price["std_err"],
+            "err_vs_oracle_over_K": err,
+            "fp64": {"value": units * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "price": fp64_price,
+                     "mixed_over_fp64": fp64_ms / ms_per_step},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 64},
+            "gpu_launches": 3 * args.steps,
+            "roofline": dominant, "roofline_sweep": rl_sweep, "roofline_pathgen": rl_gen,
+            "clocks": ck}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(opt)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["amc", "reference"], default="amc")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_amc(args)
+
+
+if __name__ == "__main__":
+    main()

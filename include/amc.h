@@ -1,0 +1,170 @@
+/*
+ * amc.h - C ABI of the GB300 (sm_103a) quasi-Monte Carlo American option
+ * pricer.
+ *
+ * Method (Cvetanoska & Stojanovski, "Using High Performance Computing and
+ * Monte Carlo Simulation for Pricing American Options"):
+ *   - the option is Bermudan on t_j = j*T/m, j = 1..m (§III.E, §V);
+ *   - quasi-random points mapped to N(0,1) by an inverse cumulative normal
+ *     (§III.D): here 32-bit Sobol' points (Joe-Kuo direction numbers,
+ *     Gray-code order, point index = path index) with a digital XOR shift
+ *     drawn from SplitMix64(seed);
+ *   - Brownian-bridge path construction (ref. [13]): breadth-first bisection;
+ *   - the GBM step of Eq. 9, evaluated in log space;
+ *   - a backward early-exercise sweep: Longstaff-Schwartz regression
+ *     (ref. [12]; §V backward induction) by default, or the paper's own
+ *     pathwise rule (Eqs. 10-11), or no early exercise (Eqs. 6-8);
+ *   - the price is the path average (Eq. 6) discounted to t = 0.
+ *
+ * Conventions for every entry point:
+ *   - return 0 (AMC_OK) or a negative AMC_E* code; no exception crosses the
+ *     ABI; amc_strerror() names a code;
+ *   - host pointers are read or written only during the call; device
+ *     pointers ("_dev") must stay valid until the work queued on the given
+ *     stream has finished; a NULL stream means the legacy default stream;
+ *   - the context owns all scratch memory; calls on one context are
+ *     serialised by the caller, except amc_serve_*, which is thread-safe;
+ *   - option validation: S0, K, sigma, T > 0 and finite, r finite,
+ *     1 <= n_steps <= AMC_MAX_STEPS, 1 <= n_paths <= AMC_MAX_PATHS,
+ *     basis in 1..4 (LSM rule), type in {AMC_PUT, AMC_CALL}; a bad option
+ *     returns AMC_EINVAL before any device work.
+ */
+#ifndef AMC_H
+#define AMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMC_OK 0
+#define AMC_EINVAL (-1)   /* bad argument                                   */
+#define AMC_ENOMEM (-2)   /* context arena or device memory exhausted       */
+#define AMC_ECUDA (-3)    /* a CUDA runtime call failed                     */
+#define AMC_ETIMEOUT (-4) /* a device-side wait ran past its time limit     */
+#define AMC_EBUSY (-5)    /* serving admission refused (memory or slots)    */
+#define AMC_PENDING (-6)  /* serving request not finished yet               */
+#define AMC_ENOTFOUND (-7)/* unknown serving ticket                         */
+
+#define AMC_MAX_STEPS 512          /* direction-number table limit          */
+#define AMC_MAX_PATHS (1LL << 31)  /* 32-bit Sobol' point index             */
+
+enum { AMC_PUT = 0, AMC_CALL = 1 };
+/* Exercise rules: Longstaff-Schwartz regression (ref. [12]); the paper's
+ * pathwise rule, Eqs. 10-11 (an upper bound, §V); European, Eqs. 6-8.      */
+enum { AMC_RULE_LSM = 0, AMC_RULE_PAPER_UB = 1, AMC_RULE_EUROPEAN = 2 };
+/* Precision: all-FP64 paths, sums and solve; or FP32 paths with
+ * compensated (double-float) FP32 sums, FP64 solve and FP64 final price.   */
+enum { AMC_FP64 = 0, AMC_MIXED = 1 };
+
+/* One option.  72 bytes, naturally aligned.                                */
+typedef struct amc_option {
+    double S0, K, r, sigma, T; /* spot, strike, rate, volatility, maturity  */
+    int32_t n_steps;           /* m exercise dates t_j = j T / m            */
+    int32_t basis;             /* LSM basis size p: {1, x, .., x^(p-1)}, x=S/K */
+    int64_t n_paths;           /* N Sobol' points / paths                   */
+    int32_t type;              /* AMC_PUT or AMC_CALL                        */
+    int32_t rule;              /* AMC_RULE_*                                 */
+    uint64_t seed;             /* digital-shift seed                         */
+} amc_option;
+
+/* Result of one pricing.  price and std_err are at t = 0; std_err is the
+ * sample standard deviation of the discounted path values over sqrt(N);
+ * delta and vega are filled by the Greeks calls only; degenerate_dates
+ * counts LSM dates with fewer than p in-the-money paths or a Cholesky
+ * pivot <= 1e-12 after equilibration (no exercise there).                  */
+typedef struct amc_result {
+    double price, std_err, delta, vega;
+    int32_t degenerate_dates;
+    int32_t status;            /* AMC_OK or the error of this option        */
+    float ms_gen, ms_sweep;    /* device time of path generation and sweep  */
+} amc_result;
+
+/* Device result block written by the asynchronous calls: 8 doubles,
+ * [price, std_err, delta, vega, degenerate_dates, status, 0, 0].           */
+#define AMC_RES_DOUBLES 8
+
+typedef struct amc_ctx amc_ctx;
+
+/* ---------------------------------------------------------------- context */
+/* Library and error strings.  No GPU needed.                               */
+const char *amc_strerror(int code);
+int amc_version(void);
+
+/* Create a context on CUDA device `device` with a device arena of
+ * `arena_bytes` (0 = 60% of the free device memory) for path storage and
+ * scratch.  Uploads the direction-number table.  *out is set on success.  */
+int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out);
+int amc_ctx_destroy(amc_ctx *ctx);
+/* Time limit of every device-side wait (default 2 s).                      */
+int amc_ctx_set_timeout(amc_ctx *ctx, double seconds);
+/* Host-side fault injection for tests (never traps or faults the GPU):
+ *   kind 1: in the next LSM sweep, CTA 0 of the first job skips its arrival
+ *           at exercise date `arg`, so the other CTAs' waits run out and the
+ *           call returns AMC_ETIMEOUT;
+ *   kind 2: the next arena reservation fails (AMC_ENOMEM);
+ *   kind 0: clear.                                                          */
+int amc_ctx_inject(amc_ctx *ctx, int kind, int64_t arg);
+/* Bytes of the arena currently free / total.                               */
+int amc_ctx_memory(amc_ctx *ctx, size_t *free_bytes, size_t *total_bytes);
+
+/* ------------------------------------------------- host-only helpers */
+/* None of these touches a GPU.                                             */
+int amc_validate_option(const amc_option *opt);
+/* Row stride (elements) of the date-major path array S[m][ld]: n_paths
+ * rounded up to a multiple of 32.                                          */
+int64_t amc_path_ld(int64_t n_paths);
+/* Bytes of S for one option: n_steps * ld * (8 for AMC_FP64, 4 otherwise). */
+size_t amc_path_bytes(int n_steps, int64_t n_paths, int prec);
+/* Digital shifts: out[d] = high 32 bits of the d-th SplitMix64 output.     */
+int amc_digital_shifts(uint64_t seed, int n_dims, uint32_t *out);
+/* Sobol' direction numbers v_{b+1} of dims 0..n_dims-1: out[d*32 + b].    */
+int amc_sobol_directions(int n_dims, uint32_t *out);
+/* Bridge schedule in coordinate order k = 0..m-1: the date filled by
+ * coordinate k and the dates it is conditioned on (0 = W(0) = 0).          */
+int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *right);
+/* CTAs the LSM sweep gives one option of n_paths paths (a pure function of
+ * n_paths and the device's SM count), and the paths each thread owns.      */
+int amc_plan_sweep(int64_t n_paths, int sm_count, int32_t *ctas, int32_t *paths_per_thread);
+
+/* ------------------------------------ step-level calls (device buffers) */
+/* Shifted Sobol' integers x[d][i], d < n_dims, i < n_points, row stride
+ * ld >= n_points (test and inspection path; the pricer never stores them). */
+int amc_sobol(amc_ctx *ctx, int n_dims, int64_t n_points, uint64_t seed,
+              uint32_t *x_dev, int64_t ld, void *stream);
+/* Steps 1-3: paths S[j-1][i] = S_i(t_j), date-major, row stride ld >=
+ * amc_path_ld(n_paths) and a multiple of 32; S 16-byte aligned (else
+ * AMC_EINVAL); float for AMC_MIXED, double for AMC_FP64.  Entries i >=
+ * n_paths of a row are left untouched.                                     */
+int amc_generate_paths(amc_ctx *ctx, const amc_option *opt, int prec,
+                       void *S_dev, int64_t ld, void *stream);
+/* Step 4 on caller paths S (as written by amc_generate_paths), result into
+ * res_dev[AMC_RES_DOUBLES].  with_greeks != 0 also fills delta and vega
+ * (frozen exercise boundary).  Asynchronous.                               */
+int amc_sweep(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
+              int64_t ld, int with_greeks, double *res_dev, void *stream);
+/* Steps 1-4 into caller storage: amc_generate_paths then amc_sweep.        */
+int amc_price_device(amc_ctx *ctx, const amc_option *opt, int prec, void *S_dev,
+                     int64_t ld, double *res_dev, void *stream);
+
+/* --------------------------------------------------- host-level calls */
+/* Price one option (paths in the context arena), blocking; out on host.   */
+int amc_price_american(amc_ctx *ctx, double S0, double K, double r, double sigma,
+                       double T, int n_steps, int64_t n_paths, int basis, int type,
+                       uint64_t seed, int rule, int prec, amc_result *out);
+/* Price n options; each option's result equals its amc_price_american
+ * result bit for bit.  Options are grouped into arena-sized waves; within a
+ * wave path generation runs as one launch and the sweeps as one persistent
+ * launch.  Blocking; out[n] on host.                                       */
+int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
+                    amc_result *out);
+/* Price, delta and vega of n options (frozen-boundary pathwise adjoint).   */
+int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
+               double *price, double *delta, double *vega);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMC_H */

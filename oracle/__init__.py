@@ -58,7 +58,8 @@ def _lib():
         lib.orc_uniform.argtypes = [ctypes.c_uint32]
         lib.orc_uniform.restype = ctypes.c_double
         lib.orc_bridge_schedule.argtypes = [ctypes.c_int, _ip, _ip, _ip]
-        lib.orc_paths.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, _u32p, _u32p, _dp, _dp]
+        lib.orc_paths.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _u32p, _u32p,
+                                                          _dp, _dp]
         lib.orc_bs.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5
         lib.orc_bs.restype = ctypes.c_double
         lib.orc_solve_normal.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -70,6 +71,7 @@ def _lib():
                                             [ctypes.c_int, ctypes.c_int64, _dp, _dp, _i32p, _dp])
         lib.orc_crr.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int] * 3
         lib.orc_crr.restype = ctypes.c_double
+        lib.orc_threads.restype = ctypes.c_int
         _LIB = lib
     return _LIB
 
@@ -89,6 +91,11 @@ def joe_kuo_raw(m):
     if poly.shape[0] < m:
         raise ValueError("Joe-Kuo data holds %d dimensions, %d asked" % (poly.shape[0], m))
     return poly, vinit
+
+
+def threads():
+    """Threads the oracle's OpenMP loops use."""
+    return _lib().orc_threads()
 
 
 def splitmix64(seed, n):
@@ -150,13 +157,13 @@ def bridge_schedule(m):
     return date, left, right
 
 
-def paths(S0, r, sigma, T, m, N, seed, with_W=False):
-    """Steps 1-3: S of shape (m, N), S[j-1, i] = S_i(t_j); optionally W too."""
+def paths(S0, r, sigma, T, m, N, seed, with_W=False, first=0):
+    """Steps 1-3: S of shape (m, N), S[j-1, i] = S_{first+i}(t_j); optionally W too."""
     V = directions(m)
     sh = shifts(seed, m)
     S = np.empty((m, N), dtype=np.float64)
     W = np.empty((m, N), dtype=np.float64) if with_W else None
-    rc = _lib().orc_paths(S0, r, sigma, T, m, N, _ptr(V, _u32p), _ptr(sh, _u32p), _ptr(S, _dp), _ptr(W, _dp))
+    rc = _lib().orc_paths(S0, r, sigma, T, m, N, first, _ptr(V, _u32p), _ptr(sh, _u32p), _ptr(S, _dp), _ptr(W, _dp))
     if rc != 0:
         raise MemoryError("oracle path generation failed (%d)" % rc)
     return (S, W) if with_W else S

@@ -33,9 +33,22 @@
  * listed in the test-suite; every function below is pinned.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads the oracle's parallel loops use (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORC_PUT 0
 #define ORC_CALL 1
@@ -235,10 +248,11 @@ int orc_bridge_matrix(int m, double T, double *A)
  * index, dimension = bridge coordinate), digital shift, uniform, inverse
  * normal, bridge, GBM in log space (Eq. 9 iterated from S_0 = S0):
  *   S_{i,j} = S0 exp((r - sigma^2/2) t_j + sigma W_i(t_j)).
- * Output S[(j-1)*N + i], j = 1..m (date-major); optional W in the same
- * layout.  Paths are independent; OpenMP splits them in contiguous blocks,
- * each starting its Gray recurrence from the direct formula.               */
-int orc_paths(double S0, double r, double sigma, double T, int m, int64_t N,
+ * Paths first..first+N-1 are generated; output S[(j-1)*N + (i-first)],
+ * j = 1..m (date-major); optional W in the same layout.  Paths are
+ * independent; OpenMP splits them in contiguous blocks, each starting its
+ * Gray recurrence from the direct formula.                                 */
+int orc_paths(double S0, double r, double sigma, double T, int m, int64_t N, int64_t first,
               const uint32_t *V, const uint32_t *shift, double *S, double *Wout)
 {
     int *date = (int *)malloc(sizeof(int) * (size_t)m);
@@ -260,7 +274,7 @@ int orc_paths(double S0, double r, double sigma, double T, int m, int64_t N,
         double *z = (double *)malloc(sizeof(double) * (size_t)m);
         double *W = (double *)malloc(sizeof(double) * (size_t)(m + 1));
         if (!X || !z || !W) { bad |= 1; free(X); free(z); free(W); continue; }
-        orc_sobol_block(V, m, (uint64_t)i0, n, X);
+        orc_sobol_block(V, m, (uint64_t)(first + i0), n, X);
         for (int64_t t = 0; t < n; ++t) {
             int64_t i = i0 + t;
             for (int k = 0; k < m; ++k)

@@ -1,0 +1,114 @@
+// Internal declarations of the amc library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/amc.h"
+
+namespace amc {
+
+// Brownian-bridge node, in the depth-first evaluation order used by the
+// path-generation kernel.  `coord` is the Sobol' dimension that the
+// breadth-first numbering gives this node; `sl`/`sr`/`so` are slots of the
+// per-path stack (slot d holds the latest node of depth d; slot `zero_slot`
+// holds W(0) = 0).  W(t_date) = wl W(t_l) + wr W(t_r) + sdu sqrt(dt) z.
+struct NodeF {
+    int32_t coord, date;
+    int16_t sl, sr, so, pad;
+    float wl, wr, sdu, pad2;
+};
+struct NodeD {
+    int32_t coord, date;
+    int16_t sl, sr, so, pad;
+    double wl, wr, sdu;
+};
+static_assert(sizeof(NodeF) == 32, "NodeF layout");
+static_assert(sizeof(NodeD) == 40, "NodeD layout");
+
+constexpr int kMaxSlots = 12;       // depth <= 10 for m <= 512, plus the zero slot
+
+struct BridgePlan {
+    int m = 0;
+    int nslots = 0;                 // stack slots including the zero slot
+    std::vector<NodeF> nf;          // depth-first order
+    std::vector<NodeD> nd;
+};
+
+// Host tables (tables.cpp).
+int host_directions(int n_dims, uint32_t *V);
+void host_shifts(uint64_t seed, int n_dims, uint32_t *out);
+int host_bridge_bfs(int m, int32_t *date, int32_t *left, int32_t *right);
+int host_bridge_plan(int m, BridgePlan *plan);
+int host_validate(const amc_option *o);
+int64_t host_ld(int64_t n_paths);
+
+// Sweep launch plan: threads per CTA, 4-path chunks per thread, CTAs.
+constexpr int kSweepThreads = 256;
+// CTAs per SM that the LSM kernel's launch bounds guarantee for a given
+// number of 4-path chunks per thread (registers hold the per-path state).
+constexpr int sweep_ctas_per_sm(int chunks) { return chunks <= 2 ? 4 : (chunks == 4 ? 2 : 1); }
+struct SweepPlan {
+    int chunks;                     // 4-path chunks per thread (1, 2, 4 or 8)
+    int ctas;                       // CTAs for this option
+};
+int host_plan_sweep(int64_t n_paths, int sm_count, SweepPlan *p);
+
+// ----------------------------------------------------------- device jobs
+// One option as the kernels see it.  All pointers are device pointers.
+struct Job {
+    double S0, K, r, sigma, T;
+    double dt, disc, invK;          // T/m, e^{-r dt}, 1/K
+    int32_t m, p, type, rule;
+    int64_t N, ld;
+    const uint32_t *shift;          // [m]
+    const void *nodes;              // NodeF[m] or NodeD[m], depth-first order
+    int32_t nslots;
+    int32_t greeks;                 // also accumulate delta and vega
+    void *S;                        // Real S[m][ld]
+    int64_t tile_begin;             // path-generation tiles: prefix over jobs
+    int64_t n_tiles;
+    int32_t cta_begin, n_cta;       // sweep CTA group
+    int32_t chunks;                 // 4-path chunks per thread
+    int32_t inject_date;            // test fault injection (0 = off)
+    void *part;                     // cross-CTA partial sums [m][n_cta][kNV] (double-float or double)
+    uint32_t *arrive;               // [m] arrival counters (zeroed before launch)
+    void *fin;                      // [n_cta][4] final per-CTA sums
+    double *res;                    // [AMC_RES_DOUBLES]
+    int32_t *status;                // shared error word of the launch
+};
+
+constexpr int kNV = 12;             // cross-CTA values per date: 2p-1 moments + p RHS (p <= 4)
+constexpr int kPathgenThreads = 128;
+constexpr int kPathgenQ = 4;        // points per thread per tile (strided by 128)
+constexpr int kTilePoints = kPathgenThreads * kPathgenQ;
+
+// Kernel arguments, passed by value (__grid_constant__): either a device
+// array of jobs (batches) or one job held inline together with its digital
+// shifts, so a single-option call needs no host-to-device copy at all.
+struct KArgs {
+    const Job *jobs;                // device array, or nullptr: use `one`
+    int32_t n_jobs;
+    int32_t max_m;
+    int64_t total;                  // path-generation tiles over all jobs
+    const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
+    uint64_t timeout_ns;
+    Job one;
+    uint32_t shift_one[AMC_MAX_STEPS];
+};
+
+// Kernel launchers (pathgen.cu, sweep.cu).  Return a cudaError_t.
+cudaError_t launch_sobol(const uint32_t *V, int n_dims, int64_t n_points, const uint32_t *shift,
+                         uint32_t *x, int64_t ld, cudaStream_t st);
+cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t st);
+cudaError_t launch_sweep_lsm(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
+                             cudaStream_t st);
+cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
+                                  cudaStream_t st);
+cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
+
+size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
+
+}  // namespace amc

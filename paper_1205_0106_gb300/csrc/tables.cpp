@@ -1,0 +1,188 @@
+// Host-side tables and plans: Sobol' direction numbers, digital shifts,
+// Brownian-bridge schedule and its depth-first evaluation plan, option
+// validation and the sweep launch plan.  Pure host code (no CUDA calls), so
+// every function here is testable without a GPU through the C ABI.
+#include <math.h>
+#include <string.h>
+
+#include <deque>
+#include <vector>
+
+#include "internal.h"
+#include "joe_kuo_raw.h"
+
+namespace amc {
+
+// Direction numbers (Bratley & Fox recurrence on the Joe & Kuo data).  For
+// dimension d >= 1 with primitive polynomial of degree s and interior
+// coefficients a_1..a_{s-1}, the odd integers m_k (k > s) follow
+//   m_k = m_{k-s} xor 2^s m_{k-s} xor  xor_{q=1}^{s-1} 2^q a_q m_{k-q},
+// and the 32-bit direction number is v_k = m_k << (32 - k).  Dimension 0 is
+// van der Corput (all m_k = 1).  V[d*32 + b] = v_{b+1}.
+int host_directions(int n_dims, uint32_t *V) {
+    if (n_dims < 1 || n_dims > AMC_JK_DIMS) return AMC_EINVAL;
+    for (int d = 0; d < n_dims; ++d) {
+        uint64_t mk[32];
+        if (d == 0) {
+            for (int k = 0; k < 32; ++k) mk[k] = 1;
+        } else {
+            const uint32_t poly = amc_jk_poly[d];
+            int s = 31 - __builtin_clz(poly);
+            if (s < 1 || s > AMC_JK_WIDTH) return AMC_EINVAL;
+            const uint32_t a = (poly >> 1) & ((1u << (s - 1)) - 1u);
+            for (int k = 0; k < s; ++k) mk[k] = amc_jk_minit[d][k];
+            for (int k = s; k < 32; ++k) {
+                uint64_t v = mk[k - s] ^ (mk[k - s] << s);
+                for (int q = 1; q < s; ++q)
+                    if ((a >> (s - 1 - q)) & 1u) v ^= mk[k - q] << q;
+                mk[k] = v;
+            }
+        }
+        for (int b = 0; b < 32; ++b) V[d * 32 + b] = (uint32_t)(mk[b] << (31 - b));
+    }
+    return AMC_OK;
+}
+
+// Digital shift of dimension d: the high word of the d-th output of
+// SplitMix64 (Steele, Lea & Flood 2014) started from `seed`.
+void host_shifts(uint64_t seed, int n_dims, uint32_t *out) {
+    uint64_t x = seed;
+    for (int d = 0; d < n_dims; ++d) {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[d] = (uint32_t)(z >> 32);
+    }
+}
+
+// Breadth-first bridge schedule in coordinate order: coordinate 0 fills
+// t_m from W(0) = 0; then intervals are split at floor((l+r)/2),
+// breadth-first, left before right, one coordinate per split.
+int host_bridge_bfs(int m, int32_t *date, int32_t *left, int32_t *right) {
+    if (m < 1 || m > AMC_MAX_STEPS) return AMC_EINVAL;
+    int k = 0;
+    date[k] = m; left[k] = 0; right[k] = 0; ++k;
+    std::deque<std::pair<int, int>> q;
+    q.emplace_back(0, m);
+    while (!q.empty()) {
+        auto iv = q.front();
+        q.pop_front();
+        if (iv.second - iv.first < 2) continue;
+        int mid = (iv.first + iv.second) / 2;
+        date[k] = mid; left[k] = iv.first; right[k] = iv.second; ++k;
+        q.emplace_back(iv.first, mid);
+        q.emplace_back(mid, iv.second);
+    }
+    return k == m ? AMC_OK : AMC_EINVAL;
+}
+
+// Depth-first evaluation plan of the same bridge.  A node only needs the W
+// of its interval end points, which are its ancestors; with one stack slot
+// per tree depth those are always resident, so a path needs depth+2 slots
+// instead of m values of shared memory.
+int host_bridge_plan(int m, BridgePlan *plan) {
+    std::vector<int32_t> date(m), left(m), right(m);
+    int rc = host_bridge_bfs(m, date.data(), left.data(), right.data());
+    if (rc != AMC_OK) return rc;
+    std::vector<int> coord_of_date(m + 1, -1), slot_of_date(m + 1, -1);
+    for (int k = 0; k < m; ++k) coord_of_date[date[k]] = k;
+    plan->m = m;
+    plan->nf.clear();
+    plan->nd.clear();
+    int maxdepth = 0;
+    auto emit = [&](int d, int l, int r, int depth, int zero_slot) {
+        NodeD n{};
+        n.coord = coord_of_date[d];
+        n.date = d;
+        n.so = (int16_t)depth;
+        if (depth == 0) {                               // W(t_m) = sqrt(t_m) z_0
+            n.sl = n.sr = (int16_t)zero_slot;
+            n.wl = n.wr = 0.0;
+            n.sdu = sqrt((double)m);
+        } else {
+            n.sl = (int16_t)(l == 0 ? zero_slot : slot_of_date[l]);
+            n.sr = (int16_t)(r == 0 ? zero_slot : slot_of_date[r]);
+            n.wl = (double)(r - d) / (double)(r - l);
+            n.wr = (double)(d - l) / (double)(r - l);
+            n.sdu = sqrt((double)(d - l) * (double)(r - d) / (double)(r - l));
+        }
+        slot_of_date[d] = depth;
+        plan->nd.push_back(n);
+    };
+    // first pass: depth of the tree
+    std::vector<std::pair<std::pair<int, int>, int>> st;
+    st.push_back({{0, m}, 1});
+    while (!st.empty()) {
+        auto e = st.back();
+        st.pop_back();
+        int l = e.first.first, r = e.first.second;
+        if (r - l < 2) continue;
+        if (e.second > maxdepth) maxdepth = e.second;
+        int mid = (l + r) / 2;
+        st.push_back({{mid, r}, e.second + 1});
+        st.push_back({{l, mid}, e.second + 1});
+    }
+    const int zero_slot = maxdepth + 1;
+    plan->nslots = zero_slot + 1;
+    if (plan->nslots > kMaxSlots) return AMC_EINVAL;
+    emit(m, 0, 0, 0, zero_slot);
+    // second pass: depth-first, left subtree first
+    st.push_back({{0, m}, 1});
+    while (!st.empty()) {
+        auto e = st.back();
+        st.pop_back();
+        int l = e.first.first, r = e.first.second;
+        if (r - l < 2) continue;
+        int mid = (l + r) / 2;
+        emit(mid, l, r, e.second, zero_slot);
+        st.push_back({{mid, r}, e.second + 1});
+        st.push_back({{l, mid}, e.second + 1});
+    }
+    if ((int)plan->nd.size() != m) return AMC_EINVAL;
+    for (const NodeD &n : plan->nd) {
+        NodeF f{};
+        f.coord = n.coord; f.date = n.date; f.sl = n.sl; f.sr = n.sr; f.so = n.so;
+        f.wl = (float)n.wl; f.wr = (float)n.wr; f.sdu = (float)n.sdu;
+        plan->nf.push_back(f);
+    }
+    return AMC_OK;
+}
+
+int host_validate(const amc_option *o) {
+    if (!o) return AMC_EINVAL;
+    auto pos = [](double v) { return isfinite(v) && v > 0.0; };
+    if (!pos(o->S0) || !pos(o->K) || !pos(o->sigma) || !pos(o->T) || !isfinite(o->r)) return AMC_EINVAL;
+    if (o->n_steps < 1 || o->n_steps > AMC_MAX_STEPS) return AMC_EINVAL;
+    if (o->n_paths < 1 || o->n_paths > AMC_MAX_PATHS) return AMC_EINVAL;
+    if (o->type != AMC_PUT && o->type != AMC_CALL) return AMC_EINVAL;
+    if (o->rule != AMC_RULE_LSM && o->rule != AMC_RULE_PAPER_UB && o->rule != AMC_RULE_EUROPEAN)
+        return AMC_EINVAL;
+    if (o->rule == AMC_RULE_LSM && (o->basis < 1 || o->basis > 4)) return AMC_EINVAL;
+    return AMC_OK;
+}
+
+int64_t host_ld(int64_t n_paths) { return (n_paths + 31) / 32 * 32; }
+
+// CTAs of kSweepThreads threads, each thread owning `chunks` groups of 4
+// consecutive paths: the fewest chunks per thread (1, 2, 4, 8) whose CTA
+// count fits the co-resident capacity sweep_ctas_per_sm(chunks) * SMs.
+// Depends on n_paths and the SM count only, so an option's reduction order
+// is the same alone or batched.
+int host_plan_sweep(int64_t n_paths, int sm_count, SweepPlan *p) {
+    if (n_paths < 1 || sm_count < 1) return AMC_EINVAL;
+    for (int c = 1; c <= 8; c *= 2) {
+        const int64_t cap = (int64_t)sweep_ctas_per_sm(c) * sm_count;
+        const int64_t per_cta = (int64_t)kSweepThreads * 4 * c;
+        const int64_t g = (n_paths + per_cta - 1) / per_cta;
+        if (g <= cap) {
+            p->chunks = c;
+            p->ctas = (int)g;
+            return AMC_OK;
+        }
+    }
+    return AMC_EINVAL;                                // too many paths to keep in registers
+}
+
+}  // namespace amc

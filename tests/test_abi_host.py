@@ -1,0 +1,102 @@
+"""C-ABI library on the CPU: it loads, exports every function include/amc.h
+declares, and its host-side logic (direction numbers, digital shifts, bridge
+schedule, validation, launch plan) is right.  No compute call needs a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def amc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1205_0106_gb300 as amc
+    return amc
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "amc.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"\b(amc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(amc):
+    names = _declared()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(amc.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(amc.SIGNATURES), set(names) - set(amc.SIGNATURES)
+
+
+def test_strerror_and_version(amc):
+    assert amc.strerror(0) == "ok"
+    assert "timed out" in amc.strerror(amc.AMC_ETIMEOUT)
+    assert amc.amc_version() >= 1
+
+
+@pytest.mark.parametrize("m", [1, 2, 50, 252, 512])
+def test_library_direction_numbers_reproduce_scipy_sobol(amc, m):
+    from scipy.stats import qmc
+    V = amc.amc_sobol_directions(m).astype(np.uint64)
+    n = 256
+    ref = np.round(qmc.Sobol(d=m, scramble=False, bits=32).random(n) * 2.0 ** 32).astype(np.uint64).T
+    i = np.arange(n, dtype=np.uint64)
+    g = i ^ (i >> 1)
+    X = np.zeros((m, n), dtype=np.uint64)
+    for b in range(32):
+        X ^= np.where(((g >> b) & 1)[None, :] == 1, V[:, b:b + 1], 0)
+    np.testing.assert_array_equal(X, ref)
+
+
+def test_library_shifts_are_splitmix64_high_words(amc):
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", "splitmix64_seed0.json")) as f:
+        g = json.load(f)
+    sh = amc.amc_digital_shifts(0, 3)
+    assert [int(s) for s in sh] == [int(h, 16) >> 32 for h in g["outputs_hex"]]
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 16, 50, 252, 365, 512])
+def test_library_bridge_schedule(amc, m):
+    d, l, r = amc.amc_bridge_schedule(m)
+    assert sorted(d.tolist()) == list(range(1, m + 1)) and d[0] == m
+    seen = {0, m}
+    for k in range(1, m):
+        assert l[k] in seen and r[k] in seen and l[k] < d[k] < r[k] and d[k] == (l[k] + r[k]) // 2
+        seen.add(int(d[k]))
+    if m == 16:
+        assert d.tolist() == [16, 8, 4, 12, 2, 6, 10, 14, 1, 3, 5, 7, 9, 11, 13, 15]
+
+
+def test_validation(amc):
+    import workloads
+    good = workloads.single_small()
+    assert amc.amc_validate_option(good) == 0
+    for field, bad in [("S0", 0.0), ("K", -1.0), ("sigma", float("nan")), ("T", 0.0), ("r", float("inf")),
+                       ("n_steps", 0), ("n_steps", 513), ("n_paths", 0), ("basis", 5), ("type", 2), ("rule", 3)]:
+        d = good.as_dict()
+        d[field] = bad
+        assert amc.amc_validate_option(d) == amc.AMC_EINVAL, field
+
+
+def test_path_layout(amc):
+    assert amc.amc_path_ld(1) == 32 and amc.amc_path_ld(32) == 32 and amc.amc_path_ld(33) == 64
+    assert amc.amc_path_bytes(252, 2 ** 20, amc.AMC_MIXED) == 252 * 2 ** 20 * 4
+    assert amc.amc_path_bytes(50, 1000, amc.AMC_FP64) == 50 * 1024 * 8
+
+
+def test_sweep_plan_is_a_function_of_paths(amc):
+    for n in [1, 1000, 2 ** 14, 2 ** 18, 2 ** 20, 2 ** 20 + 7]:
+        ctas, ppt = amc.amc_plan_sweep(n, 152)
+        assert ctas * 256 * ppt >= n
+        assert ctas * 256 * ppt < n + 256 * ppt + 1
+        assert ppt in (4, 8, 16, 32)
+    assert amc.amc_plan_sweep(2 ** 20, 152) == (512, 8)
+    with pytest.raises(amc.AmcError):
+        amc.amc_plan_sweep(2 ** 31, 152)

@@ -1,0 +1,249 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars:
+  Sobol' integers                      bit-exact
+  paths, FP64 path                     rtol 1e-11
+  paths, mixed (FP32) path             rtol 2e-5 (FP32 inverse normal,
+                                       bridge and ex2; derivation in the design doc)
+  prices (every rule, both precisions) |dP| <= 2e-4 K on identical points
+  repeated runs, batch vs single       bit-identical
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amc():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1205_0106_gb300 as amc
+    return amc
+
+
+@pytest.fixture(scope="module")
+def ctx(amc):
+    c = amc.Context(0, arena_bytes=12 << 30)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _gpu_paths(amc, ctx, torch, opt, prec):
+    ld = amc.amc_path_ld(opt.n_paths)
+    dt = torch.float64 if prec == amc.AMC_FP64 else torch.float32
+    S = torch.full((opt.n_steps, ld), float("nan"), dtype=dt, device="cuda")
+    amc.amc_generate_paths(ctx, opt, prec, S)
+    torch.cuda.synchronize()
+    return S[:, :opt.n_paths].double().cpu().numpy()
+
+
+def _gpu_price(amc, ctx, opt, prec):
+    return amc.amc_price_american(ctx, opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths,
+                                  opt.basis, opt.type, opt.seed, opt.rule, prec)
+
+
+def _oracle_price(opt):
+    return oracle.price(opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, basis=opt.basis,
+                        type=opt.type, seed=opt.seed, rule=opt.rule)
+
+
+# ------------------------------------------------------------------ Sobol'
+@pytest.mark.parametrize("m,n,seed", [(50, 2 ** 14 + 5, 1), (252, 4099, 2), (365, 1000, 7), (512, 777, 3),
+                                      (1, 33, 0)])
+def test_sobol_bit_exact(amc, ctx, torch, m, n, seed):
+    x = torch.zeros((m, n), dtype=torch.int32, device="cuda")
+    amc.amc_sobol(ctx, m, n, seed, x)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, oracle.sobol(n, m, seed=seed))
+
+
+def test_sobol_full_size_sampled_blocks(amc, ctx, torch):
+    m, n, seed = 252, 2 ** 20, 2
+    x = torch.zeros((m, n), dtype=torch.int32, device="cuda")
+    amc.amc_sobol(ctx, m, n, seed, x)
+    torch.cuda.synchronize()
+    V = oracle.directions(m)
+    for i0 in [0, 511, 2 ** 19 - 3, 777777, n - 64]:
+        blk = x[:, i0:i0 + 64].cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(blk, oracle.sobol(64, m, i0=i0, seed=seed, V=V))
+
+
+# ------------------------------------------------------------------ paths
+PATH_CASES = [
+    workloads.scaled(workloads.single_small(), n_paths=2 ** 14 + 37),
+    workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 252, 5000, basis=4, seed=2),
+    workloads.Option(90.0, 100.0, 0.03, 0.45, 2.0, 365, 2048, seed=9, type=1),
+    workloads.Option(100.0, 95.0, 0.01, 0.1, 0.25, 512, 1000, seed=5),
+    workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 100, seed=4),
+    workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 2, 33, seed=4),
+]
+
+
+@pytest.mark.parametrize("idx", range(len(PATH_CASES)))
+def test_paths_fp64_vs_oracle(amc, ctx, torch, idx):
+    opt = PATH_CASES[idx]
+    got = _gpu_paths(amc, ctx, torch, opt, amc.AMC_FP64)
+    ref = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("idx", range(len(PATH_CASES)))
+def test_paths_mixed_vs_oracle(amc, ctx, torch, idx):
+    opt = PATH_CASES[idx]
+    got = _gpu_paths(amc, ctx, torch, opt, amc.AMC_MIXED)
+    ref = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    rel = np.abs(got / ref - 1.0)
+    assert np.isfinite(got).all()
+    assert rel.max() < 2e-5, rel.max()
+
+
+def test_paths_full_size_sampled(amc, ctx, torch):
+    opt = workloads.single_large()
+    for prec, tol in ((amc.AMC_MIXED, 2e-5), (amc.AMC_FP64, 1e-11)):
+        got = _gpu_paths(amc, ctx, torch, opt, prec)
+        for first in [0, 123456, opt.n_paths - 300]:
+            ref = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, 300, opt.seed, first=first)
+            rel = np.abs(got[:, first:first + 300] / ref - 1.0)
+            assert rel.max() < tol, (prec, first, rel.max())
+
+
+# ------------------------------------------------------------------ prices
+PRICE_CASES = [
+    ("single_small_lsm", workloads.single_small()),
+    ("single_small_paper", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 50, 2 ** 14, seed=1, rule=1)),
+    ("single_small_euro", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 50, 2 ** 14, seed=1, rule=2)),
+    ("ragged_call_p2", workloads.Option(105.0, 100.0, 0.04, 0.25, 0.75, 7, 12345, basis=2, type=1, seed=11)),
+    ("ragged_put_p4", workloads.Option(95.0, 100.0, 0.07, 0.35, 1.5, 100, 30001, basis=4, seed=12)),
+    ("one_date", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 4096, seed=13)),
+    ("one_date_paper", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 4096, seed=13, rule=1)),
+    ("two_dates_p1", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 2, 1000, basis=1, seed=14)),
+    ("many_dates", workloads.Option(100.0, 110.0, 0.02, 0.4, 2.0, 365, 8192, basis=3, seed=15)),
+    ("max_dates", workloads.Option(100.0, 90.0, 0.05, 0.2, 1.0, 512, 3000, basis=3, seed=16)),
+    ("tiny_paths", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 10, 5, basis=3, seed=17)),
+    ("deep_otm_degenerate", workloads.Option(200.0, 40.0, 0.06, 0.2, 1.0, 20, 2000, basis=3, seed=18)),
+    ("big_group", workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 60, 2 ** 19 + 3, basis=4, seed=19)),
+]
+
+
+@pytest.mark.parametrize("name,opt", PRICE_CASES, ids=[c[0] for c in PRICE_CASES])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_price_vs_oracle(amc, ctx, name, opt, prec):
+    ref = _oracle_price(opt)
+    got = _gpu_price(amc, ctx, opt, prec)
+    assert got["status"] == 0
+    assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+    assert got["degenerate_dates"] == ref["degenerate_dates"]
+    assert abs(got["std_err"] - ref["std_err"]) <= 1e-3 * max(ref["std_err"], 1e-12) + 2e-4 * opt.K
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_price_full_size_vs_oracle(amc, ctx, prec):
+    opt = workloads.single_large()
+    ref = _oracle_price(opt)
+    got = _gpu_price(amc, ctx, opt, prec)
+    assert got["status"] == 0
+    assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+
+
+# ------------------------------------------------------------------ invariants
+def test_run_to_run_bit_identical(amc, ctx):
+    for opt in (workloads.single_small(), workloads.scaled(workloads.single_large(), n_paths=2 ** 18)):
+        a = _gpu_price(amc, ctx, opt, amc.AMC_MIXED)
+        b = _gpu_price(amc, ctx, opt, amc.AMC_MIXED)
+        assert a["price"] == b["price"] and a["std_err"] == b["std_err"]
+
+
+def test_batch_equals_single(amc, ctx):
+    opts = [c[1] for c in PRICE_CASES if c[1].n_paths <= 2 ** 16] + workloads.batch_options(n=6)
+    opts = [workloads.scaled(o, n_paths=min(o.n_paths, 2 ** 15)) for o in opts]
+    for prec in (amc.AMC_MIXED, amc.AMC_FP64):
+        batch = amc.amc_price_batch(ctx, opts, prec)
+        for o, b in zip(opts, batch):
+            s = _gpu_price(amc, ctx, o, prec)
+            assert b["price"] == s["price"] and b["std_err"] == s["std_err"], (o, b, s)
+
+
+def test_device_entry_points_match_host_call(amc, ctx, torch):
+    opt = workloads.single_small()
+    for prec in (amc.AMC_MIXED, amc.AMC_FP64):
+        ld = amc.amc_path_ld(opt.n_paths)
+        S = torch.empty((opt.n_steps, ld), dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        amc.amc_price_device(ctx, opt, prec, S, res)
+        torch.cuda.synchronize()
+        dev = amc.res_to_dict(res.cpu().numpy())
+        host = _gpu_price(amc, ctx, opt, prec)
+        assert dev["price"] == host["price"]
+
+
+# ------------------------------------------------------------------ Greeks
+def test_greeks_vs_oracle_pathwise(amc, ctx):
+    opts = [workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 10, 2 ** 14, basis=3, seed=5),
+            workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 25, 2 ** 13, basis=4, seed=6, rule=2),
+            workloads.Option(110.0, 100.0, 0.02, 0.25, 0.5, 12, 5000, basis=3, type=1, seed=7)]
+    for prec, tol in ((amc.AMC_FP64, 1e-9), (amc.AMC_MIXED, 2e-3)):
+        p, d, v = amc.amc_greeks(ctx, opts, prec)
+        for k, o in enumerate(opts):
+            g = oracle.greeks(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
+                              seed=o.seed, rule=o.rule)
+            assert abs(p[k] - g["price"]) <= 2e-4 * o.K
+            assert abs(d[k] - g["delta"]) <= tol + 5e-4, (prec, k, d[k], g["delta"])
+            assert abs(v[k] - g["vega"]) <= tol * 100 + 5e-2 * max(1.0, abs(g["vega"])) * (prec == 1) + 1e-6, \
+                (prec, k, v[k], g["vega"])
+
+
+def test_greeks_vs_central_differences(amc, ctx):
+    o = workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 10, 2 ** 16, basis=3, seed=5)
+    p, d, v = amc.amc_greeks(ctx, [o], amc.AMC_FP64)
+    bS, bv = 1e-3 * o.S0, 1e-3 * o.sigma
+    f = lambda **kw: _gpu_price(amc, ctx, workloads.Option(**{**o.as_dict(), **kw}), amc.AMC_FP64)["price"]
+    fd_d = (f(S0=o.S0 + bS) - f(S0=o.S0 - bS)) / (2 * bS)
+    fd_v = (f(sigma=o.sigma + bv) - f(sigma=o.sigma - bv)) / (2 * bv)
+    assert abs(d[0] - fd_d) < 0.02 * abs(fd_d) + 5e-3
+    assert abs(v[0] - fd_v) < 0.05 * abs(fd_v) + 0.2
+
+
+# ------------------------------------------------------------------ failures
+def test_device_wait_timeout_is_reported_and_context_survives(amc, ctx):
+    opt = workloads.scaled(workloads.single_large(), n_paths=2 ** 18, n_steps=20)
+    ctx.set_timeout(0.02)
+    try:
+        ctx.inject(1, 7)
+        with pytest.raises(amc.AmcError) as ei:
+            _gpu_price(amc, ctx, opt, amc.AMC_MIXED)
+        assert ei.value.code == amc.AMC_ETIMEOUT
+    finally:
+        ctx.set_timeout(2.0)
+    ok = _gpu_price(amc, ctx, workloads.single_small(), amc.AMC_MIXED)
+    assert ok["status"] == 0 and abs(ok["price"] - 4.46) < 0.05
+
+
+def test_allocation_failure_is_reported(amc, ctx):
+    ctx.inject(2)
+    with pytest.raises(amc.AmcError) as ei:
+        _gpu_price(amc, ctx, workloads.single_small(), amc.AMC_MIXED)
+    assert ei.value.code == amc.AMC_ENOMEM
+    assert _gpu_price(amc, ctx, workloads.single_small(), amc.AMC_MIXED)["status"] == 0
+
+
+def test_invalid_arguments_rejected_before_device_work(amc, ctx):
+    bad = workloads.scaled(workloads.single_small(), n_steps=0)
+    with pytest.raises(amc.AmcError) as ei:
+        _gpu_price(amc, ctx, bad, amc.AMC_MIXED)
+    assert ei.value.code == amc.AMC_EINVAL
+    with pytest.raises(amc.AmcError):
+        amc.amc_greeks(ctx, [workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 5, 100, rule=1)], amc.AMC_MIXED)
