@@ -351,8 +351,10 @@ int orc_solve_normal(int p, const double *G, const double *b, double *beta)
 
 /* ------------------------------------------------------------------------ */
 /* Longstaff-Schwartz backward sweep (ref. [12]; backward induction of §V)
- * on the date-major paths S[(j-1)*N + i].  With x = S/K and basis
- * phi = (1, x, ..., x^{p-1}):
+ * on the date-major paths S[(j-1)*N + i].  With the moneyness y = S/K - 1
+ * and basis phi = (1, y, ..., y^{p-1}) (the same function space as
+ * {1, S, ..., S^{p-1}}, so the same least-squares fit; centred so that the
+ * in-the-money y lie in (-1, 0) for puts and (0, inf) for calls):
  *   CF_i = h(S_{i,m}), tau_i = m;
  *   for j = m-1 .. 1:
  *     CF_i <- CF_i e^{-r dt};
@@ -394,9 +396,9 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
         for (int64_t i = 0; i < N; ++i) {
             double h = orc_payoff(type, Sj[i], K);
             if (!(h > 0.0)) continue;
-            double x = Sj[i] / K, phi[8];
+            double y = Sj[i] / K - 1.0, phi[8];
             phi[0] = 1.0;
-            for (int k = 1; k < p; ++k) phi[k] = phi[k - 1] * x;
+            for (int k = 1; k < p; ++k) phi[k] = phi[k - 1] * y;
             for (int k = 0; k < p; ++k) {
                 for (int l = 0; l < p; ++l) G[k * p + l] += phi[k] * phi[l];
                 b[k] += phi[k] * CF[i];
@@ -413,8 +415,8 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
         for (int64_t i = 0; i < N; ++i) {
             double h = orc_payoff(type, Sj[i], K);
             if (!(h > 0.0)) continue;
-            double x = Sj[i] / K, c = 0.0, xk = 1.0;
-            for (int k = 0; k < p; ++k) { c += beta[k] * xk; xk *= x; }
+            double y = Sj[i] / K - 1.0, c = 0.0, yk = 1.0;
+            for (int k = 0; k < p; ++k) { c += beta[k] * yk; yk *= y; }
             if (h > c) { CF[i] = h; tau[i] = j; }
         }
     }

@@ -10,8 +10,11 @@ with the C oracle entry by entry.
 import numpy as np
 
 
-def lsm_micro(S, type_, K, r, T, p):
-    """S: (m, N) date-major paths.  Returns dict(price, beta (m,p), tau, cf, degenerate)."""
+def lsm_micro(S, type_, K, r, T, p, center=1.0):
+    """S: (m, N) date-major paths.  Regression basis 1, y, .., y^(p-1) with
+    y = S/K - center (center 1: the oracle's moneyness basis; center 0: the
+    plain S/K monomials, which span the same functions).  Returns
+    dict(price, beta (m,p), tau, cf, degenerate)."""
     S = np.asarray(S, dtype=np.float64)
     m, N = S.shape
     dt = T / m
@@ -28,7 +31,7 @@ def lsm_micro(S, type_, K, r, T, p):
         if itm.size < p:
             degenerate += 1
             continue
-        x = S[j - 1, itm] / K
+        x = S[j - 1, itm] / K - center
         X = np.vander(x, p, increasing=True)
         if np.linalg.matrix_rank(X) < p:
             degenerate += 1

@@ -193,9 +193,16 @@ def test_lsm_longstaff_schwartz_worked_example():
     res = oracle.lsm(S, oracle.PUT, g["K"], g["r"], g["T"], 3, details=True)
     assert abs(res["price"] - g["value"]) < g["value_tol"]
     K = g["K"]
-    scale = np.array([1.0, K, K * K])             # basis in x = S/K -> basis in S
-    np.testing.assert_allclose(res["beta"][1] / scale, g["regression_t2_in_S"], atol=g["coef_tol"])
-    np.testing.assert_allclose(res["beta"][0] / scale, g["regression_t1_in_S"], atol=g["coef_tol"])
+    # basis in y = S/K - 1  ->  coefficients of 1, S, S^2
+    P = np.polynomial.polynomial
+    def to_S(b):
+        c = np.zeros(3)
+        for k in range(3):
+            t = P.polypow([-1.0, 1.0 / K], k)
+            c[:len(t)] += b[k] * t
+        return c
+    np.testing.assert_allclose(to_S(res["beta"][1]), g["regression_t2_in_S"], atol=g["coef_tol"])
+    np.testing.assert_allclose(to_S(res["beta"][0]), g["regression_t1_in_S"], atol=g["coef_tol"])
     # stopping dates: 0 in the fixture means never exercised (our tau = m with zero payoff)
     h = np.maximum(K - S, 0.0)
     stop = [0 if h[t - 1, i] == 0 else t for i, t in enumerate(res["tau"])]
@@ -222,6 +229,18 @@ def test_lsm_micro_oracle_on_sobol_paths():
     b = lsm_micro(S, oracle.PUT, 40.0, .06, 1.0, 3)
     assert abs(a["price"] - b["price"]) < 1e-12
     np.testing.assert_array_equal(a["tau"], b["tau"])
+
+
+def test_lsm_basis_choice_does_not_change_the_estimator():
+    # {1, y, y^2} with y = S/K - 1 and {1, x, x^2} with x = S/K span the same
+    # functions: same fitted values, same stopping dates, same price
+    S = oracle.paths(100.0, .05, .3, 1.0, 12, 4096, seed=8)
+    a = lsm_micro(S, oracle.PUT, 100.0, .05, 1.0, 3, center=1.0)
+    b = lsm_micro(S, oracle.PUT, 100.0, .05, 1.0, 3, center=0.0)
+    c = oracle.lsm(S, oracle.PUT, 100.0, .05, 1.0, 3, details=True)
+    np.testing.assert_array_equal(a["tau"], b["tau"])
+    np.testing.assert_array_equal(a["tau"], c["tau"])
+    assert abs(a["price"] - b["price"]) < 1e-12 and abs(a["price"] - c["price"]) < 1e-12
 
 
 def _rqmc(fn, R=16, base=1000):
