@@ -49,11 +49,12 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
     return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -105,38 +106,62 @@ __device__ __forceinline__ int find_job_by_cta(const Job *__restrict__ jobs, int
 
 // Equilibrated Cholesky solve of G beta = R with G_kl = M_{k+l}: scale by
 // D^{-1/2}, D = diag(G); any pivot <= 1e-12 (or a non-positive diagonal)
-// makes the date degenerate (false).
-__device__ bool solve_normal(int p, const double *M, const double *R, double *beta) {
-    double sc[4], L[4][4], y[4], g[4];
-    for (int k = 0; k < p; ++k) {
+// makes the date degenerate (false).  FP64, straight-line for a fixed basis
+// size; square roots and divisions are replaced by reciprocal square roots
+// (sqrt(a) = a rsqrt(a)) because FP64 division and square root are long
+// instruction sequences on this part and the solve sits on the per-date
+// critical path.
+template <int P>
+__device__ __forceinline__ bool solve_normal_t(const double *M, const double *R, double *beta) {
+    double sc[P], L[P][P], il[P], y[P], g[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
         const double d = M[2 * k];
         if (!(d > 0.0)) return false;
-        sc[k] = 1.0 / sqrt(d);
+        sc[k] = rsqrt(d);
     }
-    for (int k = 0; k < p; ++k) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
         for (int l = 0; l <= k; ++l) {
             double a = M[k + l] * sc[k] * sc[l];
+#pragma unroll
             for (int q = 0; q < l; ++q) a -= L[k][q] * L[l][q];
             if (l == k) {
                 if (!(a > 1e-12)) return false;
-                L[k][k] = sqrt(a);
+                il[k] = rsqrt(a);
+                L[k][k] = a * il[k];
             } else {
-                L[k][l] = a / L[l][l];
+                L[k][l] = a * il[l];
             }
         }
     }
-    for (int k = 0; k < p; ++k) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
         double a = R[k] * sc[k];
+#pragma unroll
         for (int q = 0; q < k; ++q) a -= L[k][q] * y[q];
-        y[k] = a / L[k][k];
+        y[k] = a * il[k];
     }
-    for (int k = p - 1; k >= 0; --k) {
+#pragma unroll
+    for (int k = P - 1; k >= 0; --k) {
         double a = y[k];
-        for (int q = k + 1; q < p; ++q) a -= L[q][k] * g[q];
-        g[k] = a / L[k][k];
+#pragma unroll
+        for (int q = k + 1; q < P; ++q) a -= L[q][k] * g[q];
+        g[k] = a * il[k];
     }
-    for (int k = 0; k < p; ++k) beta[k] = g[k] * sc[k];
+#pragma unroll
+    for (int k = 0; k < P; ++k) beta[k] = g[k] * sc[k];
     return true;
+}
+
+__device__ bool solve_normal(int p, const double *M, const double *R, double *beta) {
+    switch (p) {
+        case 1: return solve_normal_t<1>(M, R, beta);
+        case 2: return solve_normal_t<2>(M, R, beta);
+        case 3: return solve_normal_t<3>(M, R, beta);
+        default: return solve_normal_t<4>(M, R, beta);
+    }
 }
 
 template <bool FP64>
@@ -167,17 +192,17 @@ __device__ __forceinline__ double load_part_d(const void *part, int64_t idx) {
 
 constexpr int kWarps = kSweepThreads / 32;
 
-// Block sum of NVAL per-thread values: warp shuffle tree in the working
-// precision, then the warp partials in fixed order in double-float (mixed)
-// or double.  Result valid in threads 0..NVAL-1 (value index = thread).
+// Block sum of the per-thread values v[k] whose bit k is set in `mask`:
+// warp shuffle tree in the working precision, then the warp partials in
+// fixed order in double-float (mixed) or double.  Result in thread k.
 template <bool FP64, int NVAL>
-__device__ __forceinline__ void block_sum(typename SW<FP64>::Real (&v)[NVAL], void *s_warp, int nv,
+__device__ __forceinline__ void block_sum(typename SW<FP64>::Real (&v)[NVAL], void *s_warp, uint32_t mask,
                                           dfl *out_df, double *out_d) {
     using Real = typename SW<FP64>::Real;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NVAL; ++k) {
-        if (k < nv) {
+        if ((mask >> k) & 1) {
 #pragma unroll
             for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
         }
@@ -186,10 +211,10 @@ __device__ __forceinline__ void block_sum(typename SW<FP64>::Real (&v)[NVAL], vo
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NVAL; ++k)
-            if (k < nv) sw[w * NVAL + k] = v[k];
+            if ((mask >> k) & 1) sw[w * NVAL + k] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < nv) {
+    if (threadIdx.x < NVAL && ((mask >> threadIdx.x) & 1)) {
         const int k = threadIdx.x;
         if (FP64) {
             double a = 0.0;
@@ -218,7 +243,8 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
     const uint64_t timeout_ns = a.timeout_ns;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lc = blockIdx.x - J.cta_begin, G = J.n_cta;
-    const int m = J.m, p = J.p, nmom = 2 * p - 1, nv = 3 * p - 1;
+    const int m = J.m, p = J.p, nmom = 2 * p - 1;
+    const uint32_t vmask = ((1u << nmom) - 1u) | (((1u << p) - 1u) << 7);   // used value slots
     const bool put = J.type == AMC_PUT;
     const Real K = (Real)J.K, invK = (Real)J.invK, disc = (Real)J.disc;
     const Real *__restrict__ S = reinterpret_cast<const Real *>(J.S);
@@ -226,6 +252,8 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
     const int64_t gt = (int64_t)lc * kSweepThreads + tid, TT = (int64_t)G * kSweepThreads;
     void *part = J.part;
     int32_t *status = J.status;
+    uint32_t *const arrive = J.arrive;
+    const int inject_date = (lc == 0 && jb == 0) ? J.inject_date : 0;
 
     Real cf[P];
     int tau[GREEKS ? P : 1];
@@ -267,39 +295,35 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
                 cf[q] *= disc;
                 const Real h = payoff(put, s[q], K);
                 if (valid && h > Real(0)) {
-                    const Real x = s[q] * invK;
-                    Real xp = Real(1);
+                    const Real y = s[q] * invK - Real(1);
+                    Real yp = Real(1);
 #pragma unroll
                     for (int k = 0; k < 7; ++k) {
-                        if (k < nmom) th[k] += xp;
-                        if (k < p) th[7 + k] += xp * cf[q];
-                        xp *= x;
+                        if (k < nmom) th[k] += yp;
+                        if (k < p) th[7 + k] += yp * cf[q];
+                        yp *= y;
                     }
                 }
             }
         }
-        // compact to [moments 0..nmom-1, rhs 0..p-1]
-        Real vals[kNV - 1];
-#pragma unroll
-        for (int k = 0; k < kNV - 1; ++k) vals[k] = th[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < p) vals[nmom + k] = th[7 + k];
+        // fixed slots: moments 0..6 (first nmom used), RHS 7..10 (first p used)
         dfl mydf;
         double myd;
-        block_sum<FP64, kNV - 1>(vals, s_warp, nv, &mydf, &myd);
-        if (tid < nv) {
+        block_sum<FP64, kNV - 1>(th, s_warp, vmask, &mydf, &myd);
+        if (tid < kNV - 1 && ((vmask >> tid) & 1)) {
             const int64_t idx = ((int64_t)(j - 1) * G + lc) * kNV + tid;
             if (FP64) store_part(part, idx, myd); else store_part(part, idx, mydf);
             __threadfence();
         }
         __syncthreads();
         if (tid == 0) {
+            // arrive (release: this CTA's partials are visible first), then
+            // poll with relaxed loads and take one acquire fence at the end
             int flag = 0;
-            uint32_t *arr = J.arrive + (j - 1);
-            if (!(J.inject_date == j && lc == 0 && jb == 0)) red_release_add(arr, 1u);
+            uint32_t *arr = arrive + (j - 1);
+            if (inject_date != j) red_release_add(arr, 1u);
             const uint64_t t0 = globaltimer();
-            while (ld_acquire(arr) < (uint32_t)G) {
+            while (ld_relaxed(arr) < (uint32_t)G) {
                 if (ld_volatile_int(status) != 0) { flag = 1; break; }
                 if (globaltimer() - t0 > timeout_ns) {
                     atomicCAS(status, 0, AMC_ETIMEOUT);
@@ -307,12 +331,14 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
                     break;
                 }
             }
+            fence_acq_rel_gpu();
             s_flag = flag;
         }
         __syncthreads();
         if (s_flag) return;
         // every CTA reduces all partials of this date in the same fixed order
-        for (int v = wid; v < nv; v += kWarps) {
+        for (int v = wid; v < kNV - 1; v += kWarps) {
+            if (!((vmask >> v) & 1)) continue;
             const int64_t base = (int64_t)(j - 1) * G * kNV + v;
             if (FP64) {
                 double a = 0.0;
@@ -336,7 +362,7 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
         __syncthreads();
         if (tid == 0) {
             double beta[4] = {0, 0, 0, 0};
-            bool ok = s_tot[0] >= (double)p && solve_normal(p, s_tot, s_tot + nmom, beta);
+            bool ok = s_tot[0] >= (double)p && solve_normal(p, s_tot, s_tot + 7, beta);
             for (int k = 0; k < 4; ++k) s_beta[k] = beta[k];
             s_flag = ok ? 0 : 2;
         }
@@ -356,11 +382,11 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
                 const bool valid = 4 * (gt + c * TT) + e < N;
                 const Real h = payoff(put, s[q], K);
                 if (valid && h > Real(0)) {
-                    const Real x = s[q] * invK;
+                    const Real y = s[q] * invK - Real(1);
                     Real cont = b[3];
-                    cont = cont * x + b[2];
-                    cont = cont * x + b[1];
-                    cont = cont * x + b[0];
+                    cont = cont * y + b[2];
+                    cont = cont * y + b[1];
+                    cont = cont * y + b[0];
                     if (h > cont) {
                         cf[q] = h;
                         if (GREEKS) { tau[q] = j; st[q] = s[q]; }
@@ -394,7 +420,7 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
     }
     dfl fdf;
     double fd;
-    block_sum<FP64, 4>(fsum, s_warp, 4, &fdf, &fd);
+    block_sum<FP64, 4>(fsum, s_warp, 0xFu, &fdf, &fd);
     if (tid < 4) {
         double* fin = reinterpret_cast<double *>(J.fin);
         fin[(int64_t)lc * 4 + tid] = FP64 ? fd : (double)fdf.hi + (double)fdf.lo;
@@ -503,7 +529,7 @@ sweep_pathwise_kernel(const __grid_constant__ KArgs a) {
     }
     dfl fdf;
     double fd;
-    block_sum<FP64, 4>(fsum, s_warp, 4, &fdf, &fd);
+    block_sum<FP64, 4>(fsum, s_warp, 0xFu, &fdf, &fd);
     if (tid < 4) {
         double* fin = reinterpret_cast<double *>(J.fin);
         fin[(int64_t)lc * 4 + tid] = FP64 ? fd : (double)fdf.hi + (double)fdf.lo;
