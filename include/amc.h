@@ -164,6 +164,31 @@ int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
 int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                double *price, double *delta, double *vega);
 
+/* ------------------------------------------- allocation-free sweep */
+/* Step 4 (as amc_sweep) without a context and without allocating device
+ * memory.  The paper has no counterpart: this entry point exists for
+ * callers that may not allocate, e.g. a host framework that owns the whole
+ * device-memory budget and forbids libraries to grow it, or a latency-
+ * critical loop that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or a plugin hook that holds no amc_ctx (creating one
+ * allocates).  The caller passes the paths S_dev (as written by
+ * amc_generate_paths) and the result block res_dev[AMC_RES_DOUBLES].
+ *   Scratch: a file-scope device array of amc_sweep_noalloc_capacity()
+ * bytes (16 MiB) that every GPU loading the library holds until exit.  An
+ * option needs 256 + 4*AMC_MAX_STEPS + 32*2048 + 96*n_steps*C bytes of it,
+ * C = the CTA count amc_plan_sweep gives (252 dates with 2^20 paths fit;
+ * 512 dates with 2^20 paths do not); larger options return AMC_EINVAL
+ * before any device work.
+ *   The first call on a device looks up the array's device address and the
+ * SM count (no allocation) and should come before any stream capture.
+ * Every call on a device shares the array and clears its counters itself;
+ * calls whose work overlaps on the GPU (other streams, or other host
+ * threads) race on it and must be serialised by the caller.  Uses the
+ * current device; same results as amc_sweep.                               */
+int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_dev, int64_t ld,
+                      int with_greeks, double *res_dev, void *stream);
+size_t amc_sweep_noalloc_capacity(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,8 @@ SIGNATURES = {
                                           ctypes.c_int, ctypes.c_int, _resp]),
     "amc_price_batch": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _resp]),
     "amc_greeks": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "amc_sweep_noalloc": (ctypes.c_int, [_optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
+    "amc_sweep_noalloc_capacity": (ctypes.c_size_t, []),
 }
 
 
@@ -252,6 +254,18 @@ def amc_price_device(ctx, opt, prec, S, res, ld=None, stream=None):
     ld = S.shape[1] if ld is None else ld
     _check(lib().amc_price_device(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(res),
                                   _stream(stream)), "amc_price_device")
+
+
+def amc_sweep_noalloc(opt, prec, S, res, ld=None, with_greeks=False, stream=None):
+    """Sweep without a context or any device allocation (scratch in a fixed
+    device array of the library; see include/amc.h).  Uses the current device."""
+    ld = S.shape[1] if ld is None else ld
+    _check(lib().amc_sweep_noalloc(ctypes.byref(make_option(opt)), prec, _ptr(S), ld, 1 if with_greeks else 0,
+                                   _ptr(res), _stream(stream)), "amc_sweep_noalloc")
+
+
+def amc_sweep_noalloc_capacity():
+    return lib().amc_sweep_noalloc_capacity()
 
 
 def res_to_dict(res_row):

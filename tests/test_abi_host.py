@@ -22,7 +22,8 @@ def amc():
 def _declared():
     with open(os.path.join(ROOT, "include", "amc.h")) as f:
         src = f.read()
-    return sorted(set(re.findall(r"\b(amc_[a-z_0-9]+)\s*\(", src)))
+    # function declarations: a return type at the start of a line, then the name
+    return sorted(set(re.findall(r"^(?:const\s+)?[a-z_0-9]+\s*\*?\s*(amc_[a-z_0-9]+)\s*\(", src, re.M)))
 
 
 def test_exports_every_declared_function(amc):
