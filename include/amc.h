@@ -125,9 +125,13 @@ int amc_sobol_directions(int n_dims, uint32_t *out);
 /* Bridge schedule in coordinate order k = 0..m-1: the date filled by
  * coordinate k and the dates it is conditioned on (0 = W(0) = 0).          */
 int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *right);
-/* CTAs the LSM sweep gives one option of n_paths paths (a pure function of
- * n_paths and the device's SM count), and the paths each thread owns.      */
-int amc_plan_sweep(int64_t n_paths, int sm_count, int32_t *ctas, int32_t *paths_per_thread);
+/* CTAs the sweep gives one option of n_paths paths in precision `prec`
+ * under `rule` (a pure function of these and the device's SM count), and
+ * the paths each sweep thread owns.  AMC_EINVAL when the option's per-path
+ * state does not fit on chip: the mixed LSM sweep holds up to
+ * min(SMs, 160) * 7936 paths (1.2 M on 152 SMs), the other sweeps up to
+ * SMs * 8192.                                                              */
+int amc_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, int32_t *ctas, int32_t *paths_per_thread);
 
 /* ------------------------------------ step-level calls (device buffers) */
 /* Shifted Sobol' integers x[d][i], d < n_dims, i < n_points, row stride
@@ -175,10 +179,11 @@ int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
  * amc_generate_paths) and the result block res_dev[AMC_RES_DOUBLES].
  *   Scratch: a file-scope device array of amc_sweep_noalloc_capacity()
  * bytes (16 MiB) that every GPU loading the library holds until exit.  An
- * option needs 256 + 4*AMC_MAX_STEPS + 32*2048 + 96*n_steps*C bytes of it,
- * C = the CTA count amc_plan_sweep gives (252 dates with 2^20 paths fit;
- * 512 dates with 2^20 paths do not); larger options return AMC_EINVAL
- * before any device work.
+ * option needs 66,304 bytes plus its exchange data: 88*(n_steps+2)*C bytes
+ * for the mixed LSM sweep, 96*n_steps*C bytes otherwise, C = the CTA count
+ * of amc_plan_sweep (all mixed LSM options fit; an FP64 LSM option with 512
+ * dates and 2^20 paths does not); larger options return AMC_EINVAL before
+ * any device work.
  *   The first call on a device looks up the array's device address and the
  * SM count (no allocation) and should come before any stream capture.
  * Every call on a device shares the array and clears its counters itself;

@@ -69,7 +69,7 @@ SIGNATURES = {
     "amc_digital_shifts": (ctypes.c_int, [_u64, ctypes.c_int, _u32p]),
     "amc_sobol_directions": (ctypes.c_int, [ctypes.c_int, _u32p]),
     "amc_bridge_schedule": (ctypes.c_int, [ctypes.c_int, _i32p, _i32p, _i32p]),
-    "amc_plan_sweep": (ctypes.c_int, [_i64, ctypes.c_int, _i32p, _i32p]),
+    "amc_plan_sweep": (ctypes.c_int, [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p]),
     "amc_sobol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _u64, _vp, _i64, _vp]),
     "amc_generate_paths": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp]),
     "amc_sweep": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
@@ -178,9 +178,9 @@ def amc_bridge_schedule(n_steps):
     return d, l, r
 
 
-def amc_plan_sweep(n_paths, sm_count):
+def amc_plan_sweep(n_paths, sm_count, prec=AMC_MIXED, rule=AMC_RULE_LSM):
     c, p = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().amc_plan_sweep(n_paths, sm_count, ctypes.byref(c), ctypes.byref(p)), "amc_plan_sweep")
+    _check(lib().amc_plan_sweep(n_paths, sm_count, prec, rule, ctypes.byref(c), ctypes.byref(p)), "amc_plan_sweep")
     return c.value, p.value
 
 

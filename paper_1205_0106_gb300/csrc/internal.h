@@ -50,11 +50,16 @@ constexpr int kSweepThreads = 256;
 // CTAs per SM that the LSM kernel's launch bounds guarantee for a given
 // number of 4-path chunks per thread (registers hold the per-path state).
 constexpr int sweep_ctas_per_sm(int chunks) { return chunks <= 2 ? 4 : (chunks == 4 ? 2 : 1); }
+// kind 1: generic sweep kernels (sweep.cu: FP64 LSM and the pathwise
+// rules), `chunks` 4-path chunks per thread, 256 threads per CTA;
+// kind 2: mixed-precision LSM kernel (sweep_v2.cu), 7936 paths per CTA.
 struct SweepPlan {
-    int chunks;                     // 4-path chunks per thread (1, 2, 4 or 8)
+    int kind;
+    int chunks;
     int ctas;                       // CTAs for this option
 };
-int host_plan_sweep(int64_t n_paths, int sm_count, SweepPlan *p);
+int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p);
+constexpr int kV2MaxCtas = 160;
 
 // ----------------------------------------------------------- device jobs
 // One option as the kernels see it.  All pointers are device pointers.
@@ -78,9 +83,22 @@ struct Job {
     void *fin;                      // [n_cta][4] final per-CTA sums
     double *res;                    // [AMC_RES_DOUBLES]
     int32_t *status;                // shared error word of the launch
+    uint64_t *xch;                  // tagged exchange units [m+2][kXV][n_cta] (mixed LSM sweep)
 };
 
 constexpr int kNV = 12;             // cross-CTA values per date: 2p-1 moments + p RHS (p <= 4)
+
+// Mixed-precision LSM sweep (sweep_v2.cu): 1 solver warp + 31 path warps,
+// 8 paths per path thread, a ring of 5 date slices in shared memory.
+constexpr int kV2Threads = 1024;
+constexpr int kV2Workers = 992;
+constexpr int kV2PPT = 8;
+constexpr int kV2PathsPerCta = kV2Workers * kV2PPT;   // 7936
+constexpr int kV2Slots = 5;
+constexpr int kXV = 11;             // exchanged values per date: 7 moment slots + 4 RHS slots
+constexpr uint32_t kEpochBits = 22; // tag = epoch << 10 | exchange index
+inline int v2_ctas(int64_t n_paths) { return (int)((n_paths + kV2PathsPerCta - 1) / kV2PathsPerCta); }
+inline size_t v2_xch_units(int m, int ctas) { return (size_t)(m + 2) * kXV * ctas; }
 constexpr int kPathgenThreads = 128;
 constexpr int kPathgenQ = 4;        // points per thread per tile (strided by 128)
 constexpr int kTilePoints = kPathgenThreads * kPathgenQ;
@@ -95,6 +113,7 @@ struct KArgs {
     int64_t total;                  // path-generation tiles over all jobs
     const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
     uint64_t timeout_ns;
+    uint32_t epoch;                 // launch tag of the mixed LSM sweep's exchange units
     Job one;
     uint32_t shift_one[AMC_MAX_STEPS];
 };
@@ -108,6 +127,7 @@ cudaError_t launch_sweep_lsm(const KArgs &a, int total_ctas, int chunks, bool fp
 cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
                                   cudaStream_t st);
 cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
+cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 

@@ -23,7 +23,7 @@ constexpr size_t kOffStatus = 0;
 constexpr size_t kOffArrive = 256;                                  // AMC_MAX_STEPS u32
 constexpr size_t kOffFin = kOffArrive + 4 * AMC_MAX_STEPS;          // [G][4] double
 constexpr size_t kMaxFinCtas = 2048;
-constexpr size_t kOffPart = kOffFin + 32 * kMaxFinCtas;             // [m][G][kNV] 8-byte words
+constexpr size_t kOffData = kOffFin + 32 * kMaxFinCtas;             // partials [m][G][kNV] or exchange units
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -31,6 +31,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_scratch_dev[kMaxDevices];   // device address of g_noalloc_scratch, per device
 int g_sm_count[kMaxDevices];
+uint32_t g_epoch[kMaxDevices];               // launch tags of the exchange units, per device
 
 // Once per device, with that device current: look up the array's device
 // address (the host-side name is only a stand-in) and the SM count.
@@ -64,10 +65,11 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
     rc = setup_device(dev);
     if (rc != AMC_OK) return rc;
     SweepPlan pl;
-    rc = host_plan_sweep(opt->n_paths, g_sm_count[dev], &pl);
+    rc = host_plan_sweep(opt->n_paths, g_sm_count[dev], prec, opt->rule, &pl);
     if (rc != AMC_OK) return rc;
-    const size_t part_bytes = (size_t)opt->n_steps * pl.ctas * kNV * 8;
-    if ((size_t)pl.ctas > kMaxFinCtas || kOffPart + part_bytes > kNoallocBytes) return AMC_EINVAL;
+    const size_t data_bytes = pl.kind == 2 ? v2_xch_units(opt->n_steps, pl.ctas) * 8
+                                           : (size_t)opt->n_steps * pl.ctas * kNV * 8;
+    if ((size_t)pl.ctas > kMaxFinCtas || kOffData + data_bytes > kNoallocBytes) return AMC_EINVAL;
 
     unsigned char *base = g_scratch_dev[dev];
     cudaStream_t st = (cudaStream_t)stream;
@@ -92,16 +94,29 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
     J.status = reinterpret_cast<int32_t *>(base + kOffStatus);
     J.arrive = reinterpret_cast<uint32_t *>(base + kOffArrive);
     J.fin = base + kOffFin;
-    J.part = base + kOffPart;
+    J.part = base + kOffData;
+    J.xch = reinterpret_cast<uint64_t *>(base + kOffData);
     J.res = res_dev;
     a.jobs = nullptr;
     a.n_jobs = 1;
     a.max_m = opt->n_steps;
     a.timeout_ns = 2000000000ull;
-    // the array keeps the previous call's contents: clear what must start at zero
+    // the array keeps the previous call's contents: clear what must start at
+    // zero (status, arrival counters); exchange units carry a launch tag that
+    // differs from every earlier call's, and are cleared when the tag wraps
     if (cudaMemsetAsync(base, 0, kOffFin, st) != cudaSuccess) return AMC_ECUDA;
+    if (pl.kind == 2) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_epoch[dev] = (g_epoch[dev] + 1) & ((1u << kEpochBits) - 1u);
+        if (g_epoch[dev] == 0) {
+            if (cudaMemsetAsync(base + kOffData, 0, kNoallocBytes - kOffData, st) != cudaSuccess) return AMC_ECUDA;
+            g_epoch[dev] = 1;
+        }
+        a.epoch = g_epoch[dev];
+    }
     const bool fp64 = prec == AMC_FP64;
-    cudaError_t e = opt->rule == AMC_RULE_LSM
+    cudaError_t e = pl.kind == 2 ? launch_sweep_lsm_v2(a, pl.ctas, with_greeks != 0, st)
+                    : opt->rule == AMC_RULE_LSM
                         ? launch_sweep_lsm(a, pl.ctas, pl.chunks, fp64, with_greeks != 0, st)
                         : launch_sweep_pathwise(a, pl.ctas, pl.chunks, fp64, with_greeks != 0, st);
     if (e != cudaSuccess) return AMC_ECUDA;

@@ -46,6 +46,8 @@ struct amc_ctx {
     double *fin1 = nullptr;
     double *res1 = nullptr;
     int32_t *status1 = nullptr;
+    uint64_t *xch1 = nullptr;                   // exchange units of the mixed LSM sweep
+    uint32_t epoch = 0;                         // launch tag of those units
     int gcap = 0;
     double *res_host = nullptr;                 // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -117,14 +119,34 @@ void fill_job_common(const amc_option *o, Job *J) {
 
 uint64_t timeout_ns(const amc_ctx *c) { return (uint64_t)(c->timeout_s * 1e9); }
 
-// Launch the sweep of `n` packed jobs (same precision, same chunks, same
-// rule class) and their finalize; jobs_dev already holds them.
-int launch_sweeps(amc_ctx *c, KArgs &a, int total_ctas, int chunks, bool lsm, bool fp64, bool greeks,
+// Next launch tag of the mixed LSM sweep's exchange units.  Tags never
+// repeat within 2^22 launches; when the counter wraps, every buffer that
+// can hold units (the context scratch and the arena) is cleared first.
+uint32_t next_epoch(amc_ctx *c) {
+    c->epoch = (c->epoch + 1) & ((1u << kEpochBits) - 1u);
+    if (c->epoch == 0) {
+        cudaDeviceSynchronize();
+        cudaMemset(c->xch1, 0, sizeof(uint64_t) * v2_xch_units(AMC_MAX_STEPS, kV2MaxCtas));
+        cudaMemset(c->arena, 0, c->arena_bytes);
+        c->epoch = 1;
+    }
+    return c->epoch;
+}
+
+// Launch the sweep of the packed jobs in `a` (same precision, same plan
+// kind and chunk count, same rule class) and their finalize.
+int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, bool lsm, bool fp64, bool greeks,
                   cudaStream_t st) {
     a.timeout_ns = timeout_ns(c);
     cudaError_t e;
-    if (lsm) e = launch_sweep_lsm(a, total_ctas, chunks, fp64, greeks, st);
-    else e = launch_sweep_pathwise(a, total_ctas, chunks, fp64, greeks, st);
+    if (pl.kind == 2) {
+        a.epoch = next_epoch(c);
+        e = launch_sweep_lsm_v2(a, total_ctas, greeks, st);
+    } else if (lsm) {
+        e = launch_sweep_lsm(a, total_ctas, pl.chunks, fp64, greeks, st);
+    } else {
+        e = launch_sweep_pathwise(a, total_ctas, pl.chunks, fp64, greeks, st);
+    }
     AMC_TRY_CUDA(e);
     AMC_TRY_CUDA(launch_finalize(a, st));
     return AMC_OK;
@@ -174,7 +196,7 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     if (!res || ((uintptr_t)res & 7u) != 0) return AMC_EINVAL;
     if (greeks && o->rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
     SweepPlan pl;
-    AMC_TRY(host_plan_sweep(o->n_paths, c->sm_count, &pl));
+    AMC_TRY(host_plan_sweep(o->n_paths, c->sm_count, prec, o->rule, &pl));
     if (pl.ctas > c->gcap) return AMC_EINVAL;
     KArgs &a = c->args;
     memset(&a, 0, sizeof(KArgs));
@@ -191,6 +213,7 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     J.fin = c->fin1;
     J.res = res;
     J.status = c->status1;
+    J.xch = c->xch1;
     if (c->inject_kind == 1) {
         J.inject_date = (int32_t)c->inject_arg;
         c->inject_kind = 0;
@@ -199,10 +222,10 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     a.n_jobs = 1;
     a.max_m = o->n_steps;
     a.V = c->V;
-    if (o->rule == AMC_RULE_LSM)
+    if (pl.kind == 1 && o->rule == AMC_RULE_LSM)
         AMC_TRY_CUDA(cudaMemsetAsync(c->arrive1, 0, sizeof(uint32_t) * o->n_steps, st));
     AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
-    return launch_sweeps(c, a, pl.ctas, pl.chunks, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st);
+    return launch_sweeps(c, a, pl, pl.ctas, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st);
 }
 
 int result_from(const double *r, amc_result *out) {
@@ -247,12 +270,13 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     for (int i = 0; i < n; ++i) {
         Item it;
         it.idx = i;
-        AMC_TRY(host_plan_sweep(opts[i].n_paths, c->sm_count, &it.pl));
+        AMC_TRY(host_plan_sweep(opts[i].n_paths, c->sm_count, prec, opts[i].rule, &it.pl));
         it.lsm = opts[i].rule == AMC_RULE_LSM;
         items.push_back(it);
     }
-    // group by (chunks, rule class), keeping input order within a group
+    // group by (plan kind, chunks, rule class), keeping input order within a group
     std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.pl.kind != b.pl.kind) return a.pl.kind < b.pl.kind;
         if (a.pl.chunks != b.pl.chunks) return a.pl.chunks < b.pl.chunks;
         return a.lsm && !b.lsm;
     });
@@ -260,19 +284,23 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     size_t pos = 0;
     cudaStream_t st = c->stream;
     while (pos < items.size()) {
-        const int chunks = items[pos].pl.chunks;
+        const SweepPlan plan0 = items[pos].pl;
+        const int chunks = plan0.chunks;
         const bool lsm = items[pos].lsm;
-        const int cap = sweep_ctas_per_sm(chunks) * c->sm_count;
+        const int cap = plan0.kind == 2 ? std::min(c->sm_count, kV2MaxCtas)
+                                        : sweep_ctas_per_sm(chunks) * c->sm_count;
         c->arena_top = 0;
         // per-wave fixed scratch sized for the worst case of this wave
         std::vector<Item> wave;
         size_t bytes = 0;
         int ctas = 0, max_m = 1;
         size_t budget = c->arena_bytes;
-        while (pos < items.size() && items[pos].pl.chunks == chunks && items[pos].lsm == lsm) {
+        while (pos < items.size() && items[pos].pl.kind == plan0.kind && items[pos].pl.chunks == chunks &&
+               items[pos].lsm == lsm) {
             const amc_option &o = opts[items[pos].idx];
             size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);
             need += align_up((size_t)o.n_steps * items[pos].pl.ctas * kNV * 8, 256);   // partials
+            need += align_up(v2_xch_units(o.n_steps, items[pos].pl.ctas) * 8, 256);    // exchange units
             need += align_up((size_t)o.n_steps * 4, 256) * 2;                          // arrive + shifts
             need += align_up((size_t)items[pos].pl.ctas * 32, 256) + 256 + sizeof(Job) + 256;
             if (!wave.empty() && (bytes + need > budget || ctas + items[pos].pl.ctas > cap)) break;
@@ -327,7 +355,11 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
             J.chunks = chunks;
             cta += J.n_cta;
             J.greeks = greeks ? 1 : 0;
-            AMC_TRY(arena_alloc(c, (size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
+            if (plan0.kind == 2) {
+                AMC_TRY(arena_alloc(c, v2_xch_units(o.n_steps, J.n_cta) * 8, (void **)&J.xch));
+            } else {
+                AMC_TRY(arena_alloc(c, (size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
+            }
             J.arrive = arrive_all + arr_off;
             arr_off += o.n_steps;
             AMC_TRY(arena_alloc(c, (size_t)J.n_cta * 4 * sizeof(double), &J.fin));
@@ -347,7 +379,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         a.total = tiles;
         a.V = c->V;
         AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));
-        AMC_TRY(launch_sweeps(c, a, cta, chunks, lsm, fp64, greeks, st));
+        AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st));
         std::vector<double> res((size_t)nw * AMC_RES_DOUBLES);
         AMC_TRY_CUDA(cudaMemcpyAsync(res.data(), res_dev, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
         AMC_TRY_CUDA(cudaStreamSynchronize(st));
@@ -401,12 +433,12 @@ int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *righ
     if (!date || !left || !right) return AMC_EINVAL;
     return host_bridge_bfs(n_steps, date, left, right);
 }
-int amc_plan_sweep(int64_t n_paths, int sm_count, int32_t *ctas, int32_t *paths_per_thread) {
+int amc_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, int32_t *ctas, int32_t *paths_per_thread) {
     SweepPlan p;
-    int rc = host_plan_sweep(n_paths, sm_count, &p);
+    int rc = host_plan_sweep(n_paths, sm_count, prec, rule, &p);
     if (rc != AMC_OK) return rc;
     if (ctas) *ctas = p.ctas;
-    if (paths_per_thread) *paths_per_thread = 4 * p.chunks;
+    if (paths_per_thread) *paths_per_thread = p.kind == 2 ? kV2PPT : 4 * p.chunks;
     return AMC_OK;
 }
 
@@ -440,6 +472,8 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
             cudaMalloc(&c->fin1, sizeof(double) * 4 * c->gcap) != cudaSuccess ||
             cudaMalloc(&c->res1, sizeof(double) * AMC_RES_DOUBLES) != cudaSuccess ||
             cudaMalloc(&c->status1, sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->xch1, sizeof(uint64_t) * v2_xch_units(AMC_MAX_STEPS, kV2MaxCtas)) != cudaSuccess ||
+            cudaMemset(c->xch1, 0, sizeof(uint64_t) * v2_xch_units(AMC_MAX_STEPS, kV2MaxCtas)) != cudaSuccess ||
             cudaMallocHost(&c->res_host, sizeof(double) * AMC_RES_DOUBLES) != cudaSuccess) {
             rc = AMC_ENOMEM;
             break;
@@ -453,6 +487,7 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
             arena_bytes = (size_t)(fr * 0.6) / 4096 * 4096;
         }
         if (cudaMalloc(&c->arena, arena_bytes) != cudaSuccess) { rc = AMC_ENOMEM; break; }
+        if (cudaMemset(c->arena, 0, arena_bytes) != cudaSuccess) { rc = AMC_ECUDA; break; }
         c->arena_bytes = arena_bytes;
     } while (0);
     if (rc != AMC_OK) {
@@ -478,6 +513,7 @@ int amc_ctx_destroy(amc_ctx *c) {
     cudaFree(c->fin1);
     cudaFree(c->res1);
     cudaFree(c->status1);
+    cudaFree(c->xch1);
     cudaFree(c->arena);
     if (c->res_host) cudaFreeHost(c->res_host);
     for (int k = 0; k < 3; ++k)

@@ -1,0 +1,547 @@
+// Mixed-precision Longstaff-Schwartz sweep for sm_103a (ref. [12]; the
+// backward induction of §V), built around the per-date latency chain.
+//
+// One CTA of 1024 threads per SM: warp 0 is the solver, warps 1..31 own
+// 8 paths per thread (7936 paths per CTA, a contiguous slice of every date
+// row).  Per CTA:
+//   - a ring of 5 date slices in shared memory, filled by TMA bulk copies
+//     (cp.async.bulk + mbarrier) up to 5 dates ahead of use, so HBM latency
+//     never sits on the critical path;
+//   - the in-the-money Gram moments M_k = sum y^k (y = S/K - 1) depend on
+//     the paths only, so they are summed from the ring and exchanged two
+//     dates before they are needed; the solver warp turns each date's
+//     totals into the inverse Gram matrix in FP64 (16 cofactors in
+//     parallel; the degenerate-date test on the equilibrated Cholesky
+//     pivots is decided from leading principal minors) while the path
+//     warps work on later dates;
+//   - what is left on the critical path per date: CF *= e^{-r dt}, the
+//     right-hand sides R_k = sum y^k CF, a warp-shuffle + double-float block
+//     sum, the cross-CTA exchange, beta = Ginv R in FP64 (16 lanes) and the
+//     exercise update h > phi(y).beta.
+// Cross-CTA exchange: every CTA writes its partial of each value as one
+// 64-bit unit (FP32 payload, 32-bit tag = launch epoch and exchange index)
+// and every CTA polls all units of that value until every tag matches, then
+// adds them in a fixed order in double-float: one L2 round trip, no counter,
+// and bit-identical totals in all CTAs.  Every wait (ring slots, exchange,
+// solver hand-off) is bounded by %globaltimer; on expiry the CTA records
+// AMC_ETIMEOUT, the others see it, and each CTA waits (bounded) for its own
+// copies in flight before it returns.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "devutil.cuh"
+#include "internal.h"
+
+namespace amc {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kT = kV2Threads;
+constexpr int kWorkers = kV2Workers;
+constexpr int kPPT = kV2PPT;
+constexpr int kPPC = kV2PathsPerCta;
+constexpr int kSlots = kV2Slots;
+constexpr int kMaxCtas = 160;               // exchange gather: 5 units per lane
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SmemV2 {
+    float S[kSlots][kPPC];
+    uint64_t mbar[kSlots];
+    float redG[2][32][7];           // warp sums of Gram moments, by exchange parity
+    float redR[32][4];              // warp sums of right-hand sides
+    float red[32][4];               // final sums
+    double tot[kXV];
+    double gtot[3][8];
+    double ginv[3][16];
+    double beta[4];
+    double sA[16];
+    double sP[4];
+    int gdeg[3];
+    int deg_cur;                    // degenerate flag of the coefficients in beta
+    int pend[kSlots];
+    volatile int gready;
+    volatile int ginv_ready;
+    volatile int abort;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_work() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+// Barrier of the path warps that also ORs a flag over them: every path
+// thread gets the same answer, so all leave the loop together.
+__device__ __forceinline__ bool bar_work_any(bool flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "n"(kWorkers)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(b))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void st_unit(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_unit(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int find_job_by_cta(const Job *__restrict__ jobs, int n_jobs, int cta) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cta_begin <= cta) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Solver warp: inverse of the p x p Gram matrix G_kl = M_{k+l} (identity
+// beyond p) as the transposed cofactor matrix over the determinant, lane
+// 4k+l computing cofactor (k, l); G is symmetric, so is its inverse.  The
+// matrix is first scaled by exact powers of two, A = P G P, which changes
+// no rounding.  Degenerate date test: the q-th Cholesky pivot of the
+// equilibrated matrix D^{-1/2} G D^{-1/2} (D = diag G) equals
+//   det(G_{q+1}) / (det(G_q) G_qq)
+// with G_q the leading q x q block, so "pivot <= 1e-12" is decided from
+// leading principal minors (lanes 16..18) without divisions or square
+// roots.  Every FP64 chain here is a handful of operations deep, against
+// a long sequential chain for a Cholesky factorisation.
+__device__ __forceinline__ double det3(double a00, double a01, double a02, double a10, double a11, double a12,
+                                       double a20, double a21, double a22) {
+    return a00 * fma(a11, a22, -a12 * a21) - a01 * fma(a10, a22, -a12 * a20) + a02 * fma(a10, a21, -a11 * a20);
+}
+
+__device__ __forceinline__ double gram_inverse(const double *M, int p, int lane, double *sA, double *sP,
+                                               bool &deg) {
+    // power-of-two scale factors P_k ~ 1/sqrt(M_2k) (exact), scaled matrix in shared memory
+    if (lane < 4) {
+        int e = 0;
+        if (lane < p && M[2 * lane] > 0.0) frexp(M[2 * lane], &e);
+        sP[lane] = ldexp(1.0, -(e / 2));
+    }
+    __syncwarp();
+    if (lane < 16) {
+        const int r = lane >> 2, c = lane & 3;
+        sA[lane] = (r < p && c < p) ? M[r + c] * sP[r] * sP[c] : (r == c ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    const int k = (lane >> 2) & 3, l = lane & 3;
+    // cofactor (k, l): rows != k, cols != l
+    const int r0 = k == 0 ? 1 : 0, r1 = k <= 1 ? 2 : 1, r2 = k <= 2 ? 3 : 2;
+    const int c0 = l == 0 ? 1 : 0, c1 = l <= 1 ? 2 : 1, c2 = l <= 2 ? 3 : 2;
+    const double minor = det3(sA[4 * r0 + c0], sA[4 * r0 + c1], sA[4 * r0 + c2], sA[4 * r1 + c0], sA[4 * r1 + c1],
+                              sA[4 * r1 + c2], sA[4 * r2 + c0], sA[4 * r2 + c1], sA[4 * r2 + c2]);
+    const double cof = ((k + l) & 1) ? -minor : minor;
+    // det = sum_l A[0][l] C_0l (lanes 0..3), same value in every lane
+    double t = lane < 4 ? sA[lane] * cof : 0.0;
+    t += __shfl_xor_sync(kFull, t, 1);
+    t += __shfl_xor_sync(kFull, t, 2);
+    const double det = __shfl_sync(kFull, t, 0);
+    // leading principal minors det(A_1..A_3); det(A_4) = det
+    const double d1 = sA[0];
+    const double d2 = fma(sA[0], sA[5], -sA[1] * sA[4]);
+    const double d3 = det3(sA[0], sA[1], sA[2], sA[4], sA[5], sA[6], sA[8], sA[9], sA[10]);
+    bool bad = !(M[0] >= (double)p);
+    if (p >= 1 && !(d1 > 1e-12 * sA[0])) bad = true;
+    if (p >= 2 && !(d2 > 1e-12 * d1 * sA[5])) bad = true;
+    if (p >= 3 && !(d3 > 1e-12 * d2 * sA[10])) bad = true;
+    if (p >= 4 && !(det > 1e-12 * d3 * sA[15])) bad = true;
+    deg = bad;
+    // 1/det: single-precision seed, two Newton steps in FP64
+    double rd = (double)__frcp_rn((float)det);
+    rd = rd * fma(-det, rd, 2.0);
+    rd = rd * fma(-det, rd, 2.0);
+    return (k < p && l < p) ? cof * rd * sP[k] * sP[l] : 0.0;
+}
+
+template <bool GREEKS>
+__global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_constant__ KArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemV2 &sm = *reinterpret_cast<SmemV2 *>(smem_raw);
+    const int jb = a.jobs ? find_job_by_cta(a.jobs, a.n_jobs, blockIdx.x) : 0;
+    const Job &J = a.jobs ? a.jobs[jb] : a.one;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lc = blockIdx.x - J.cta_begin, G = J.n_cta;
+    const int m = J.m, p = J.p, nmom = 2 * p - 1;
+    const bool put = J.type == AMC_PUT;
+    const float K = (float)J.K, invK = (float)J.invK, disc = (float)J.disc;
+    const float *__restrict__ S = reinterpret_cast<const float *>(J.S);
+    const int64_t N = J.N, ld = J.ld;
+    const int64_t base = (int64_t)lc * kPPC;
+    const int64_t rem = ld - base;
+    const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * 4u;
+    uint64_t *const xch = J.xch;
+    int32_t *const status = J.status;
+    const uint64_t timeout_ns = a.timeout_ns;
+    const uint32_t tag_hi = a.epoch << 10;
+    const int inject_date = (lc == 0 && jb == 0) ? J.inject_date : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&sm.mbar[s], 1);
+            sm.pend[s] = 0;
+        }
+        sm.gready = m + 1;
+        sm.ginv_ready = m + 1;
+        sm.deg_cur = 0;
+        for (int k = 0; k < 4; ++k) sm.beta[k] = 0.0;
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------ solver warp
+    if (warp == 0) {
+        for (int d = m - 1; d >= 1; --d) {
+            const uint64_t t0 = globaltimer();
+            bool bail = false;
+            while (sm.gready > d) {
+                if (sm.abort || ld_volatile_int(status) != 0 || globaltimer() - t0 > timeout_ns) {
+                    bail = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            bail = __any_sync(kFull, bail);
+            if (bail) {
+                if (lane == 0) {
+                    atomicCAS(status, 0, AMC_ETIMEOUT);
+                    sm.abort = 1;
+                }
+                return;
+            }
+            __threadfence_block();
+            const int b = d % 3;
+            bool deg;
+            const double gi = gram_inverse(sm.gtot[b], p, lane, sm.sA, sm.sP, deg);
+            if (lane < 16) sm.ginv[b][lane] = gi;
+            if (lane == 0) sm.gdeg[b] = deg ? 1 : 0;
+            __syncwarp();
+            __threadfence_block();
+            if (lane == 0) sm.ginv_ready = d;
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------ path warps
+    const int w = tid - 32;
+    auto issue = [&](int d) {            // w == 0 only
+        const int s = d % kSlots;
+        fence_proxy_async();
+        mbar_expect(&sm.mbar[s], slice_bytes);
+        bulk_load(sm.S[s], S + (int64_t)(d - 1) * ld + base, slice_bytes, &sm.mbar[s]);
+        sm.pend[s] = d;
+    };
+    auto wait_slice = [&](int d) -> bool {
+        const int s = d % kSlots;
+        const uint32_t parity = (uint32_t)((m - d) / kSlots) & 1u;
+        const uint64_t t0 = globaltimer();
+        while (!mbar_test(&sm.mbar[s], parity)) {
+            if (sm.abort || globaltimer() - t0 > timeout_ns) {
+                atomicCAS(status, 0, AMC_ETIMEOUT);
+                sm.abort = 1;
+                return false;
+            }
+        }
+        if (w == 0) sm.pend[s] = 0;
+        return true;
+    };
+    // validity of the own paths (ragged last CTA), fixed for the whole sweep
+    uint32_t valid = 0;
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i)
+        if (base + w + i * kWorkers < N) valid |= 1u << i;
+    // in-the-money Gram moments of date d over the own paths, summed over
+    // the warp and left in sm.redG[buf][warp][k] for a later exchange
+    auto gram_post = [&](int d, int buf) {
+        float g[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) g[k] = 0.f;
+        const float *sl = sm.S[d % kSlots];
+#pragma unroll
+        for (int i = 0; i < kPPT; ++i) {
+            const float s = sl[w + i * kWorkers];
+            const float h = payoff(put, s, K);
+            if (((valid >> i) & 1u) && h > 0.f) {
+                const float y = fmaf(s, invK, -1.f);
+                float yp = 1.f;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    if (k < nmom) g[k] += yp;
+                    yp *= y;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            if (k < nmom) {
+#pragma unroll
+                for (int off = 16; off; off >>= 1) g[k] += __shfl_xor_sync(kFull, g[k], off);
+                if (lane == 0) sm.redG[buf][warp][k] = g[k];
+            }
+        }
+    };
+
+    if (w == 0)
+        for (int d = m; d >= 1 && d > m - kSlots; --d) issue(d);
+
+    float cf[kPPT];
+    int tau[GREEKS ? kPPT : 1];
+    float st[GREEKS ? kPPT : 1];
+    int degenerate = 0;
+    const bool ok = wait_slice(m);
+    if (ok) {
+        const float *sl = sm.S[m % kSlots];
+#pragma unroll
+        for (int i = 0; i < kPPT; ++i) {
+            const float s = sl[w + i * kWorkers];
+            cf[i] = ((valid >> i) & 1u) ? payoff(put, s, K) : 0.f;
+            if (GREEKS) { tau[i] = m; st[i] = s; }
+        }
+    }
+    bool stop = bar_work_any(!ok || sm.abort);
+    if (w == 0 && m - kSlots >= 1 && !stop) issue(m - kSlots);
+    // Gram moments of date m-1, posted at the first exchange (index m+1)
+    if (m >= 2 && !stop && wait_slice(m - 1)) gram_post(m - 1, (m + 1) & 1);
+
+    // exercise at date d with the coefficients in sm.beta (fused into the
+    // right-hand-side pass of the next date)
+    auto exercise = [&](int d, int i, float b0, float b1, float b2, float b3) {
+        const float s = sm.S[d % kSlots][w + i * kWorkers];
+        const float h = payoff(put, s, K);
+        if (((valid >> i) & 1u) && h > 0.f) {
+            const float y = fmaf(s, invK, -1.f);
+            const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+            if (h > cont) {
+                cf[i] = h;
+                if (GREEKS) { tau[i] = d; st[i] = s; }
+            }
+        }
+    };
+
+    for (int j = m + 1; j >= 1 && !stop; --j) {
+        const bool hasR = j <= m - 1;
+        const bool hasG = j - 2 >= 1;
+        float rr[4] = {0.f, 0.f, 0.f, 0.f};
+        if (hasR) {
+            // exercise at j+1 (coefficients of the previous exchange), then
+            // discount to t_j and sum the right-hand sides of date j
+            const bool ex = j + 1 <= m - 1 && !sm.deg_cur;
+            const float b0 = (float)sm.beta[0], b1 = (float)sm.beta[1];
+            const float b2 = (float)sm.beta[2], b3 = (float)sm.beta[3];
+            const float *sl = sm.S[j % kSlots];
+#pragma unroll
+            for (int i = 0; i < kPPT; ++i) {
+                if (ex) exercise(j + 1, i, b0, b1, b2, b3);
+                cf[i] *= disc;
+                const float s = sl[w + i * kWorkers];
+                const float h = payoff(put, s, K);
+                if (((valid >> i) & 1u) && h > 0.f) {
+                    const float y = fmaf(s, invK, -1.f);
+                    const float c = cf[i];
+                    rr[0] += c;
+                    rr[1] = fmaf(c, y, rr[1]);
+                    const float y2 = y * y;
+                    rr[2] = fmaf(c, y2, rr[2]);
+                    rr[3] = fmaf(c, y2 * y, rr[3]);
+                }
+            }
+            if (j + 1 <= m - 1 && sm.deg_cur && w == 0) ++degenerate;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < p) {
+#pragma unroll
+                    for (int off = 16; off; off >>= 1) rr[k] += __shfl_xor_sync(kFull, rr[k], off);
+                    if (lane == 0) sm.redR[warp][k] = rr[k];
+                }
+            }
+        }
+        const uint32_t mask = (hasG ? ((1u << nmom) - 1u) : 0u) | (hasR ? (((1u << p) - 1u) << 7) : 0u);
+        bar_work();                                               // B1
+        if (w == 0 && j + 1 <= m - 1 && j + 1 - kSlots >= 1) issue(j + 1 - kSlots);   // slice j+1 consumed
+        // cross-CTA exchange: warp 1+k owns value slot k; it posts first, then
+        // computes its share of the next Gram moments, then gathers
+        const uint32_t tag = tag_hi | (uint32_t)j;
+        const bool xw = warp >= 1 && warp <= kXV && ((mask >> (warp - 1)) & 1u);
+        const int xk = warp - 1;
+        uint64_t *xu = xch + ((size_t)j * kXV + (xw ? xk : 0)) * G;
+        if (xw) {
+            const float pv = lane < 31 ? (xk < 7 ? sm.redG[j & 1][lane + 1][xk] : sm.redR[lane + 1][xk - 7]) : 0.f;
+            dfl part = df_warp_sum(dfl{pv, 0.f});
+            if (lane == 0 && inject_date != j)
+                st_unit(xu + lc, ((uint64_t)tag << 32) | __float_as_uint(__fadd_rn(part.hi, part.lo)));
+        }
+        // Gram moments of date j-3, posted at the next exchange
+        if (j - 3 >= 1 && !sm.abort && wait_slice(j - 3)) gram_post(j - 3, (j - 1) & 1);
+        if (xw) {
+            float vals[kMaxCtas / 32];
+            const uint64_t t0 = globaltimer();
+            for (;;) {
+                bool good = true;
+#pragma unroll
+                for (int q = 0; q < kMaxCtas / 32; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < G) {
+                        const uint64_t u = ld_unit(xu + c);
+                        if ((uint32_t)(u >> 32) != tag) good = false;
+                        vals[q] = __uint_as_float((uint32_t)u);
+                    }
+                }
+                if (__all_sync(kFull, good)) break;
+                bool bail = sm.abort || ld_volatile_int(status) != 0 || globaltimer() - t0 > timeout_ns;
+                if (__any_sync(kFull, bail)) {
+                    if (lane == 0) {
+                        atomicCAS(status, 0, AMC_ETIMEOUT);
+                        sm.abort = 1;
+                    }
+                    break;
+                }
+            }
+            dfl acc = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < kMaxCtas / 32; ++q)
+                if (lane + 32 * q < G) acc = df_add(acc, dfl{vals[q], 0.f});
+            acc = df_warp_sum(acc);
+            if (lane == 0) sm.tot[xk] = (double)acc.hi + (double)acc.lo;
+        }
+        stop = bar_work_any(sm.abort);                            // B2
+        if (stop) break;
+        if (hasG && w == 0) {                                     // Gram totals of date j-2 -> solver
+            const int b = (j - 2) % 3;
+            for (int k = 0; k < 7; ++k) sm.gtot[b][k] = sm.tot[k];
+            __threadfence_block();
+            sm.gready = j - 2;
+        }
+        if (hasR) {
+            if (warp == 1) {
+                const uint64_t t0 = globaltimer();
+                bool bail = false;
+                while (sm.ginv_ready > j) {
+                    if (sm.abort || globaltimer() - t0 > timeout_ns) {
+                        bail = true;
+                        break;
+                    }
+                }
+                if (bail && lane == 0) {
+                    atomicCAS(status, 0, AMC_ETIMEOUT);
+                    sm.abort = 1;
+                }
+                __threadfence_block();
+                const int b = j % 3;
+                // beta_k = sum_l Ginv_kl R_l: lane 4k+l one product, then two butterfly steps
+                const int bl = lane & 3;
+                double t = (lane < 16 && bl < p) ? sm.ginv[b][lane] * sm.tot[7 + bl] : 0.0;
+                t += __shfl_xor_sync(kFull, t, 1);
+                t += __shfl_xor_sync(kFull, t, 2);
+                if (lane < 16 && bl == 0) sm.beta[lane >> 2] = t;
+                if (lane == 0) sm.deg_cur = sm.gdeg[b];
+            }
+            stop = bar_work_any(sm.abort);                        // B3
+            if (stop) break;
+        }
+    }
+    // the last exercise date, t_1
+    if (!stop && m >= 2) {
+        if (sm.deg_cur) {
+            if (w == 0) ++degenerate;
+        } else {
+            const float b0 = (float)sm.beta[0], b1 = (float)sm.beta[1];
+            const float b2 = (float)sm.beta[2], b3 = (float)sm.beta[3];
+#pragma unroll
+            for (int i = 0; i < kPPT; ++i) exercise(1, i, b0, b1, b2, b3);
+        }
+    }
+
+    if (stop) {
+        // bounded wait for this CTA's own copies still in flight, then leave
+        if (w == 0) {
+            for (int s = 0; s < kSlots; ++s) {
+                const int d = sm.pend[s];
+                if (d <= 0) continue;
+                const uint32_t parity = (uint32_t)((m - d) / kSlots) & 1u;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_test(&sm.mbar[s], parity) && globaltimer() - t0 < timeout_ns) {
+                }
+            }
+        }
+        return;
+    }
+
+    // final per-CTA sums: CF, CF^2, delta, vega (discounting to 0 in finalize)
+    float fs[4] = {0.f, 0.f, 0.f, 0.f};
+    const float S0 = (float)J.S0, r = (float)J.r, sig = (float)J.sigma, dt = (float)J.dt;
+    const float mu = r - 0.5f * sig * sig;
+#pragma unroll
+    for (int i = 0; i < kPPT; ++i) {
+        const int li = w + i * kWorkers;
+        if (base + li >= N) continue;
+        fs[0] += cf[i];
+        fs[1] += cf[i] * cf[i];
+        if (GREEKS && cf[i] > 0.f) {
+            const float t = (float)tau[i] * dt;
+            const float dfac = expf(-r * t);
+            const float dh = put ? -1.f : 1.f;
+            const float Wt = (logf(st[i] / S0) - mu * t) / sig;
+            fs[2] += dfac * dh * st[i] / S0;
+            fs[3] += dfac * dh * st[i] * (Wt - sig * t);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) fs[k] += __shfl_xor_sync(kFull, fs[k], off);
+        if (lane == 0) sm.red[warp][k] = fs[k];
+    }
+    bar_work();
+    if (warp >= 1 && warp <= 4) {
+        const int k = warp - 1;
+        dfl part = {lane < 31 ? sm.red[lane + 1][k] : 0.f, 0.f};
+        part = df_warp_sum(part);
+        if (lane == 0) reinterpret_cast<double *>(J.fin)[(int64_t)lc * 4 + k] = (double)part.hi + (double)part.lo;
+    }
+    if (lc == 0 && w == 0) J.res[4] = (double)degenerate;
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st) {
+    const void *f = greeks ? (const void *)sweep_lsm_v2_kernel<true> : (const void *)sweep_lsm_v2_kernel<false>;
+    const int smem = (int)sizeof(SmemV2);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    return cudaLaunchCooperativeKernel(f, dim3((unsigned)total_ctas), dim3(kT), args, (size_t)smem, st);
+}
+
+}  // namespace amc

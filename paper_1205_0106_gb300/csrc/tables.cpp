@@ -165,18 +165,29 @@ int host_validate(const amc_option *o) {
 
 int64_t host_ld(int64_t n_paths) { return (n_paths + 31) / 32 * 32; }
 
+// Sweep launch plan of one option.  Mixed-precision LSM: one 1024-thread
+// CTA per 7936 paths, at most one CTA per SM (co-resident).  Otherwise:
 // CTAs of kSweepThreads threads, each thread owning `chunks` groups of 4
-// consecutive paths: the fewest chunks per thread (1, 2, 4, 8) whose CTA
+// consecutive paths, the fewest chunks per thread (1, 2, 4, 8) whose CTA
 // count fits the co-resident capacity sweep_ctas_per_sm(chunks) * SMs.
-// Depends on n_paths and the SM count only, so an option's reduction order
-// is the same alone or batched.
-int host_plan_sweep(int64_t n_paths, int sm_count, SweepPlan *p) {
+// Depends on the path count, precision, rule and SM count only, so an
+// option's reduction order is the same alone or batched.
+int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p) {
     if (n_paths < 1 || sm_count < 1) return AMC_EINVAL;
+    if (prec == AMC_MIXED && rule == AMC_RULE_LSM) {
+        const int64_t g = (n_paths + kV2PathsPerCta - 1) / kV2PathsPerCta;
+        if (g > sm_count || g > kV2MaxCtas) return AMC_EINVAL;   // per-path state must stay on chip
+        p->kind = 2;
+        p->chunks = kV2PPT;
+        p->ctas = (int)g;
+        return AMC_OK;
+    }
     for (int c = 1; c <= 8; c *= 2) {
         const int64_t cap = (int64_t)sweep_ctas_per_sm(c) * sm_count;
         const int64_t per_cta = (int64_t)kSweepThreads * 4 * c;
         const int64_t g = (n_paths + per_cta - 1) / per_cta;
         if (g <= cap) {
+            p->kind = 1;
             p->chunks = c;
             p->ctas = (int)g;
             return AMC_OK;

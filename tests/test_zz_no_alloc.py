@@ -62,9 +62,9 @@ def test_noalloc_sweep_matches_context_sweep_on_two_calls(env, name, opt, prec):
 def test_noalloc_rejects_options_beyond_its_scratch(env):
     amc, ctx, torch = env
     big = workloads.scaled(workloads.single_large(), n_steps=512)
-    S = torch.empty((1, amc.amc_path_ld(big.n_paths)), dtype=torch.float32, device="cuda")
+    S = torch.empty((1, amc.amc_path_ld(big.n_paths)), dtype=torch.float64, device="cuda")
     res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
     with pytest.raises(amc.AmcError) as ei:
-        amc.amc_sweep_noalloc(big, amc.AMC_MIXED, S, res)
+        amc.amc_sweep_noalloc(big, amc.AMC_FP64, S, res)
     assert ei.value.code == amc.AMC_EINVAL
     assert amc.amc_sweep_noalloc_capacity() == 16 << 20
