@@ -209,6 +209,15 @@ def run_amc(args):
             return total, sum(gen) / steps, sum(swp) / steps, res
         return ev[0].elapsed_time(ev[1]), None, None, res
 
+    if args.profile:
+        # profiling mode: only the timed mixed-precision steps (for ncu)
+        t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": t_ms / args.steps}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     clocks = Clocks(torch.cuda.current_device())
     # headline: mixed precision, device-resident
     clocks.start()
@@ -295,8 +304,9 @@ def main():
     ap.add_argument("--impl", choices=["amc", "reference"], default="amc")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.profile:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
