@@ -140,8 +140,9 @@ int amc_sobol(amc_ctx *ctx, int n_dims, int64_t n_points, uint64_t seed,
               uint32_t *x_dev, int64_t ld, void *stream);
 /* Steps 1-3: paths S[j-1][i] = S_i(t_j), date-major, row stride ld >=
  * amc_path_ld(n_paths) and a multiple of 32; S 16-byte aligned (else
- * AMC_EINVAL); float for AMC_MIXED, double for AMC_FP64.  Entries i >=
- * n_paths of a row are left untouched.                                     */
+ * AMC_EINVAL); float for AMC_MIXED, double for AMC_FP64.  Entries
+ * n_paths <= i < ld of a row may receive the values of the extra Sobol'
+ * points; nothing beyond ld is written.                                    */
 int amc_generate_paths(amc_ctx *ctx, const amc_option *opt, int prec,
                        void *S_dev, int64_t ld, void *stream);
 /* Step 4 on caller paths S (as written by amc_generate_paths), result into

@@ -110,6 +110,8 @@ struct KArgs {
     const Job *jobs;                // device array, or nullptr: use `one`
     int32_t n_jobs;
     int32_t max_m;
+    int32_t max_slots;              // largest bridge stack over the jobs (path generation)
+    int32_t pad_;
     int64_t total;                  // path-generation tiles over all jobs
     const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
     uint64_t timeout_ns;

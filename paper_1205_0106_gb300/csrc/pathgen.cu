@@ -1,17 +1,20 @@
 // Path generation (steps 1-3 of the hot path) for sm_103a:
 //   Sobol' integers (Gray-code order, digital XOR shift)      §III.D
-//   -> uniform (x + 1/2) 2^-32 -> N(0,1)                      §III.D (Moro)
+//   -> uniform (x + 1/2) 2^-32 -> N(0,1)                      §III.D
 //   -> Brownian bridge (breadth-first coordinate order,       ref. [13]
 //      evaluated depth-first with a per-path slot stack)
 //   -> GBM in log space, S = S0 exp((r - sigma^2/2) t + sigma W)   Eq. 9
-//   -> date-major store S[j-1][i], coalesced across the warp.
+//   -> date-major store S[j-1][i].
 //
-// One CTA of 128 threads owns a tile of 512 consecutive Sobol' points; thread
-// t owns points tile + q*128 + t (q = 0..3).  Because the Gray code is
-// linear over GF(2) and these index parts occupy disjoint bits,
-//   x(tile + q*128 + t) = x(tile + q*128) xor x(t),
-// so the per-CTA part is computed once per tile (shared memory) and the
-// per-thread part needs only the low 7 direction numbers of a dimension.
+// One CTA of 128 threads owns a tile of 512 consecutive Sobol' points and
+// thread t the 4 consecutive points tile + 4t + q (q = 0..3), so every date
+// row is written with one 16-byte store per thread and the bridge stack is
+// read and written as float4.  The Gray code is linear over GF(2) and the
+// three index parts occupy disjoint bits, hence
+//   x(tile + 4t + q) = x(tile) xor x(4t) xor x(q):
+// x(tile) per dimension once per tile (shared memory), x(4t) from the
+// direction numbers v_2..v_9 selected by the thread's Gray bits, x(q) from
+// v_1, v_2 (the same for all threads).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -31,38 +34,63 @@ __device__ __forceinline__ uint32_t sobol_direct(const uint32_t *__restrict__ V,
     return x;
 }
 
-// Inverse cumulative normal in FP32 after Moro (1995): a rational function
-// of (u - 1/2)^2 for |u - 1/2| < 0.42 and a degree-8 polynomial in
-// log(-log p), p = min(u, 1 - u), in the tails.  The uniform comes straight
-// from the 32-bit integer: u - 1/2 = (x - 2^31 + 1/2) 2^-32 from the signed
-// offset, and the tail probability from x or its complement, so neither
-// rounds to 0 or 1 in single precision.
-__device__ __forceinline__ float icdf_moro(uint32_t x) {
-    const int32_t d = (int32_t)(x ^ 0x80000000u);           // x - 2^31
-    const float y = fmaf((float)d, 0x1p-32f, 0x1p-33f);      // u - 1/2
-    float z;
-    if (fabsf(y) < 0.42f) {
-        const float r = y * y;
-        const float num = fmaf(fmaf(fmaf(-25.44106049637f, r, 41.39119773534f), r, -18.61500062529f), r,
-                               2.50662823884f);
-        const float den = fmaf(fmaf(fmaf(fmaf(3.13082909833f, r, -21.06224101826f), r, 23.08336743743f), r,
-                                    -8.47351093090f), r, 1.0f);
-        z = y * __fdividef(num, den);
-    } else {
-        const uint32_t xs = (x & 0x80000000u) ? ~x : x;
-        const float p = fmaf((float)xs, 0x1p-32f, 0x1p-33f);
-        const float t = __logf(-__logf(p));
-        float c = fmaf(0.0000003960315187f, t, 0.0000002888167364f);
-        c = fmaf(c, t, 0.0000321767881768f);
-        c = fmaf(c, t, 0.0003951896511919f);
-        c = fmaf(c, t, 0.0038405729373609f);
-        c = fmaf(c, t, 0.0276438810333863f);
-        c = fmaf(c, t, 0.1607979714918209f);
-        c = fmaf(c, t, 0.9761690190917186f);
-        c = fmaf(c, t, 0.3374754822726147f);
-        z = y < 0.0f ? -c : c;
-    }
-    return z;
+// Inverse cumulative normal in FP32.  Two-region form of M. Giles
+// (GPU Computing Gems, 2010) applied to the normal quantile, with this
+// project's own coefficients (Chebyshev least-squares fit to the exact
+// quantile, fit_icdf.py; worst relative error of the float evaluation
+// 2.9e-7 over the whole 32-bit uniform grid):
+//   y = u - 1/2 from the signed offset x - 2^31 (no rounding at 0 or 1),
+//   |y| < 0.4983 (99.66 % of points): z = y A(w - 2.5), w = -log(1 - 4y^2),
+//   otherwise: z = y B(sqrt(w) - 3), w = -log(4p(1-p)), p = min(u, 1-u)
+//   taken from x or its complement so the tail keeps full precision.
+// One logarithm per point and almost no divergence inside a warp, where the
+// paper's Moro formula needs a division in the centre and two logarithms in
+// the tails.
+__device__ __forceinline__ float lg2_approx(float v) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float v) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Central region: straight-line code, valid when |u - 1/2| < 0.4983.
+__device__ __forceinline__ float icdf_central(float y) {
+    const float wc = fmaf(-0.693147181f, lg2_approx(fmaf(-4.f * y, y, 1.f)), -2.5f);
+    float a = -2.471926130e-08f;
+    a = fmaf(a, wc, 6.586265044e-08f);
+    a = fmaf(a, wc, 1.316422299e-06f);
+    a = fmaf(a, wc, -9.795854567e-06f);
+    a = fmaf(a, wc, -1.402823636e-05f);
+    a = fmaf(a, wc, 6.175783346e-04f);
+    a = fmaf(a, wc, -3.543307772e-03f);
+    a = fmaf(a, wc, -1.181544270e-02f);
+    a = fmaf(a, wc, 6.976040602e-01f);
+    a = fmaf(a, wc, 4.246626854e+00f);
+    return y * a;
+}
+// Tails: p = min(u, 1-u) from x or its complement.
+__device__ __noinline__ float icdf_tail(uint32_t x, float y) {
+    const uint32_t xs = (x & 0x80000000u) ? ~x : x;
+    const float p = fmaf((float)xs, 0x1p-32f, 0x1p-33f);
+    const float sc = sqrtf(-0.693147181f * lg2_approx(fmaf(-4.f * p, p, 4.f * p))) - 3.f;
+    float b = 9.611179121e-05f;
+    b = fmaf(b, sc, -3.932459513e-04f);
+    b = fmaf(b, sc, -1.151860997e-04f);
+    b = fmaf(b, sc, 3.614928108e-03f);
+    b = fmaf(b, sc, -1.002847217e-02f);
+    b = fmaf(b, sc, 1.631816290e-02f);
+    b = fmaf(b, sc, -2.166599594e-02f);
+    b = fmaf(b, sc, 2.668302692e-02f);
+    b = fmaf(b, sc, 2.833170176e+00f);
+    b = fmaf(b, sc, 8.012868881e+00f);
+    return y * b;
+}
+__device__ __forceinline__ float icdf_y(uint32_t x) {            // u - 1/2 from the signed offset
+    return fmaf((float)(int32_t)(x ^ 0x80000000u), 0x1p-32f, 0x1p-33f);
 }
 
 template <bool FP64>
@@ -78,6 +106,24 @@ struct PG<true> {
     using Node = NodeD;
 };
 
+// Shared-memory layout of the path-generation kernel: every sub-buffer
+// starts on a 32-byte boundary (uint4 and R4<double> accesses).
+struct PathgenSmem {
+    unsigned nodes, v, xb, W, total;
+};
+__host__ __device__ __forceinline__ unsigned al32(unsigned v) { return (v + 31u) & ~31u; }
+__host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int nslots, bool fp64) {
+    PathgenSmem L;
+    const unsigned node = fp64 ? (unsigned)sizeof(NodeD) : (unsigned)sizeof(NodeF);
+    const unsigned real = fp64 ? 8u : 4u;
+    L.nodes = 0;
+    L.v = al32(L.nodes + node * (unsigned)max_m);
+    L.xb = al32(L.v + 48u * (unsigned)max_m);
+    L.W = al32(L.xb + 4u * (unsigned)max_m);
+    L.total = L.W + real * 4u * kPathgenThreads * (unsigned)nslots;
+    return L;
+}
+
 __device__ __forceinline__ int find_job_by_tile(const Job *__restrict__ jobs, int n_jobs, int64_t tile) {
     int lo = 0, hi = n_jobs - 1;
     while (lo < hi) {
@@ -87,20 +133,30 @@ __device__ __forceinline__ int find_job_by_tile(const Job *__restrict__ jobs, in
     return lo;
 }
 
+template <typename Real>
+struct alignas(4 * sizeof(Real)) R4 {
+    Real v[4];
+};
+
 template <bool FP64>
 __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_constant__ KArgs a) {
     using Real = typename PG<FP64>::Real;
     using Node = typename PG<FP64>::Node;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(32) unsigned char smem[];
     const int max_m = a.max_m;
-    Node *s_nodes = reinterpret_cast<Node *>(smem);
-    uint32_t *s_xq = reinterpret_cast<uint32_t *>(s_nodes + max_m);      // [Q][m]
-    uint32_t *s_vt = s_xq + kPathgenQ * max_m;                            // [m][8] low direction numbers
-    Real *s_W = reinterpret_cast<Real *>(s_vt + 8 * max_m);              // [slot][Q][128]
+    const PathgenSmem L = pathgen_layout(max_m, a.max_slots, FP64);
+    Node *s_nodes = reinterpret_cast<Node *>(smem + L.nodes);
+    uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][3]: v_1..v_12 of each dim
+    uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift
+    R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);              // [slot][128]
 
     const uint32_t *__restrict__ V = a.V;
     const int tid = threadIdx.x;
-    const uint32_t gt = (uint32_t)tid ^ ((uint32_t)tid >> 1);            // Gray code of t (7 bits)
+    const uint32_t t4 = 4u * (uint32_t)tid;
+    const uint32_t g4 = t4 ^ (t4 >> 1);                                   // Gray bits 1..8 of 4t
+    uint32_t gm[8];                                                       // all-ones where bit b+1 is set
+#pragma unroll
+    for (int b = 0; b < 8; ++b) gm[b] = 0u - ((g4 >> (b + 1)) & 1u);
     int cur = -1;
     int m = 0, nslots = 0;
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
@@ -114,21 +170,22 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             nslots = J.nslots;
             const Node *gn = reinterpret_cast<const Node *>(J.nodes);
             for (int i = tid; i < m; i += kPathgenThreads) s_nodes[i] = gn[i];
-            for (int i = tid; i < m * 8; i += kPathgenThreads)
-                s_vt[i] = (i & 7) < 7 ? __ldg(V + (i >> 3) * 32 + (i & 7)) : 0u;
+            for (int i = tid; i < 3 * m; i += kPathgenThreads)
+                s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 3) * 32) + (i % 3));
             cur = jb;
         }
-        for (int i = tid; i < kPathgenQ * m; i += kPathgenThreads) {
-            const int q = i / m, k = i - q * m;
-            s_xq[i] = sobol_direct(V, k, base + (uint32_t)q * kPathgenThreads) ^ shift[k];
-        }
-        const int zero = nslots - 1;
+        for (int k = tid; k < m; k += kPathgenThreads) s_xb[k] = sobol_direct(V, k, base) ^ shift[k];
+        {
+            R4<Real> zero;
 #pragma unroll
-        for (int q = 0; q < kPathgenQ; ++q) s_W[(zero * kPathgenQ + q) * kPathgenThreads + tid] = Real(0);
+            for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
+            s_W[(nslots - 1) * kPathgenThreads + tid] = zero;
+        }
         __syncthreads();
 
-        const int64_t N = J.N, ld = J.ld;
-        Real *__restrict__ S = reinterpret_cast<Real *>(J.S);
+        const int64_t ld = J.ld;
+        const bool store = (int64_t)base + t4 < ld;                       // float4 stays inside the row
+        Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + t4;
         const double mu = J.r - 0.5 * J.sigma * J.sigma;
         const Real sqdt = (Real)sqrt(J.dt);
         const Real S0 = (Real)J.S0;
@@ -138,30 +195,59 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
 
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
-            uint32_t xt = 0;
-            const uint32_t *vt = s_vt + nd.coord * 8;
-#pragma unroll
-            for (int b = 0; b < 7; ++b)
-                if ((gt >> b) & 1u) xt ^= vt[b];
+            const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];
+            uint32_t x0 = s_xb[nd.coord];
+            x0 ^= v0.y & gm[0];
+            x0 ^= v0.z & gm[1];
+            x0 ^= v0.w & gm[2];
+            x0 ^= v1.x & gm[3];
+            x0 ^= v1.y & gm[4];
+            x0 ^= v1.z & gm[5];
+            x0 ^= v1.w & gm[6];
+            x0 ^= v2.x & gm[7];
+            const uint32_t xq[4] = {x0, x0 ^ v0.x, x0 ^ v0.x ^ v0.y, x0 ^ v0.y};
             const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
             const Real drift = mu_dt * (Real)nd.date;
-            Real *__restrict__ row = S + (int64_t)(nd.date - 1) * ld;
-            const Real *Wl = s_W + (nd.sl * kPathgenQ) * kPathgenThreads + tid;
-            const Real *Wr = s_W + (nd.sr * kPathgenQ) * kPathgenThreads + tid;
-            Real *Wo = s_W + (nd.so * kPathgenQ) * kPathgenThreads + tid;
+            const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
+            const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
+            R4<Real> Wo, So;
+            Real z[4];
+            if (FP64) {
 #pragma unroll
-            for (int q = 0; q < kPathgenQ; ++q) {
-                const uint32_t x = xt ^ s_xq[q * m + nd.coord];
-                Real z;
-                if (FP64) z = (Real)normcdfinv(((double)x + 0.5) * 0x1p-32);
-                else z = (Real)icdf_moro(x);
-                const Real W = wl * Wl[q * kPathgenThreads] + wr * Wr[q * kPathgenThreads] + sd * z;
-                Wo[q * kPathgenThreads] = W;
-                Real s;
-                if (FP64) s = S0 * (Real)exp((double)(drift + sig * W));
-                else s = S0 * exp2f((float)(drift + sig * W));
-                const int64_t i = (int64_t)base + q * kPathgenThreads + tid;
-                if (i < N) row[i] = s;
+                for (int q = 0; q < 4; ++q) z[q] = (Real)normcdfinv(((double)xq[q] + 0.5) * 0x1p-32);
+            } else {
+                // the four central-region values straight-line, then the rare tails
+                float yv[4];
+                bool tail = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    yv[q] = icdf_y(xq[q]);
+                    z[q] = (Real)icdf_central(yv[q]);
+                    tail |= !(fabsf(yv[q]) < 0.4983f);
+                }
+                if (tail) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (!(fabsf(yv[q]) < 0.4983f)) z[q] = (Real)icdf_tail(xq[q], yv[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
+                Wo.v[q] = W;
+                if (FP64) So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
+                else So.v[q] = S0 * ex2_approx((float)fma(sig, W, drift));
+            }
+            s_W[nd.so * kPathgenThreads + tid] = Wo;
+            if (store) {
+                Real *dst = S + (int64_t)(nd.date - 1) * ld;
+                if (FP64) {                                               // two 16-byte stores
+                    reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
+                    reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
+                } else {
+                    *reinterpret_cast<float4 *>(dst) = make_float4((float)So.v[0], (float)So.v[1],
+                                                                   (float)So.v[2], (float)So.v[3]);
+                }
             }
         }
     }
@@ -177,13 +263,7 @@ __global__ void sobol_kernel(const uint32_t *__restrict__ V, int n_dims, int64_t
 
 }  // namespace
 
-size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64) {
-    size_t node = fp64 ? sizeof(NodeD) : sizeof(NodeF);
-    size_t real = fp64 ? 8 : 4;
-    (void)nslots;
-    return node * max_m + 4u * kPathgenQ * max_m + 4u * 8 * max_m +
-           real * kMaxSlots * kPathgenQ * kPathgenThreads;
-}
+size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64) { return pathgen_layout(max_m, nslots, fp64).total; }
 
 cudaError_t launch_sobol(const uint32_t *V, int n_dims, int64_t n_points, const uint32_t *shift,
                          uint32_t *x, int64_t ld, cudaStream_t st) {
@@ -196,7 +276,7 @@ cudaError_t launch_sobol(const uint32_t *V, int n_dims, int64_t n_points, const 
 cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t st) {
     const int64_t total_tiles = a.total;
     if (total_tiles <= 0) return cudaSuccess;
-    size_t smem = pathgen_smem_bytes(a.max_m, kMaxSlots, fp64);
+    size_t smem = pathgen_smem_bytes(a.max_m, a.max_slots, fp64);
     auto kern = fp64 ? pathgen_kernel<true> : pathgen_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -182,6 +182,7 @@ int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, 
     a.jobs = nullptr;
     a.n_jobs = 1;
     a.max_m = o->n_steps;
+    a.max_slots = b->nslots;
     a.total = J.n_tiles;
     a.V = c->V;
     AMC_TRY_CUDA(launch_pathgen(a, prec == AMC_FP64, c->sm_count, st));
@@ -334,7 +335,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         uint32_t *shift_dev;
         AMC_TRY(arena_alloc(c, sizeof(uint32_t) * shifts.size(), (void **)&shift_dev));
         int64_t tiles = 0;
-        int cta = 0;
+        int cta = 0, max_slots = 1;
         size_t arr_off = 0;
         for (int k = 0; k < nw; ++k) {
             const amc_option &o = opts[wave[k].idx];
@@ -345,6 +346,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
             J.shift = shift_dev + shift_off[k];
             J.nodes = fp64 ? (const void *)b->nd : (const void *)b->nf;
             J.nslots = b->nslots;
+            max_slots = std::max(max_slots, b->nslots);
             J.ld = host_ld(o.n_paths);
             AMC_TRY(arena_alloc(c, (size_t)o.n_steps * J.ld * esz, &J.S));
             J.tile_begin = tiles;
@@ -376,6 +378,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         a.jobs = jobs_dev;
         a.n_jobs = nw;
         a.max_m = max_m;
+        a.max_slots = max_slots;
         a.total = tiles;
         a.V = c->V;
         AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));

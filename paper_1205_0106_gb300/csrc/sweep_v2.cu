@@ -293,15 +293,19 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         for (int i = 0; i < kPPT; ++i) {
             const float s = sl[w + i * kWorkers];
             const float h = payoff(put, s, K);
-            if (((valid >> i) & 1u) && h > 0.f) {
-                const float y = fmaf(s, invK, -1.f);
-                float yp = 1.f;
-#pragma unroll
-                for (int k = 0; k < 7; ++k) {
-                    if (k < nmom) g[k] += yp;
-                    yp *= y;
-                }
-            }
+            // branch-free: weight 1 for in-the-money own paths, 0 otherwise;
+            // y is selected (not multiplied) to 0 so stale slots never reach a sum
+            const bool itm = ((valid >> i) & 1u) && h > 0.f;
+            const float one = itm ? 1.f : 0.f;
+            const float y = itm ? fmaf(s, invK, -1.f) : 0.f;
+            const float y2 = y * y, y3 = y2 * y;
+            g[0] += one;
+            g[1] = fmaf(one, y, g[1]);
+            g[2] = fmaf(one, y2, g[2]);
+            g[3] = fmaf(one, y3, g[3]);
+            g[4] = fmaf(one, y2 * y2, g[4]);
+            g[5] = fmaf(one, y2 * y3, g[5]);
+            g[6] = fmaf(one, y3 * y3, g[6]);
         }
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
@@ -340,13 +344,13 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     auto exercise = [&](int d, int i, float b0, float b1, float b2, float b3) {
         const float s = sm.S[d % kSlots][w + i * kWorkers];
         const float h = payoff(put, s, K);
-        if (((valid >> i) & 1u) && h > 0.f) {
-            const float y = fmaf(s, invK, -1.f);
-            const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
-            if (h > cont) {
-                cf[i] = h;
-                if (GREEKS) { tau[i] = d; st[i] = s; }
-            }
+        const float y = fmaf(s, invK, -1.f);
+        const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+        const bool ex = ((valid >> i) & 1u) && h > 0.f && h > cont;
+        cf[i] = ex ? h : cf[i];
+        if (GREEKS) {
+            tau[i] = ex ? d : tau[i];
+            st[i] = ex ? s : st[i];
         }
     };
 
@@ -361,21 +365,23 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             const float b0 = (float)sm.beta[0], b1 = (float)sm.beta[1];
             const float b2 = (float)sm.beta[2], b3 = (float)sm.beta[3];
             const float *sl = sm.S[j % kSlots];
+            if (ex) {                                             // uniform: keep the loop body branch-free
+#pragma unroll
+                for (int i = 0; i < kPPT; ++i) exercise(j + 1, i, b0, b1, b2, b3);
+            }
 #pragma unroll
             for (int i = 0; i < kPPT; ++i) {
-                if (ex) exercise(j + 1, i, b0, b1, b2, b3);
                 cf[i] *= disc;
                 const float s = sl[w + i * kWorkers];
                 const float h = payoff(put, s, K);
-                if (((valid >> i) & 1u) && h > 0.f) {
-                    const float y = fmaf(s, invK, -1.f);
-                    const float c = cf[i];
-                    rr[0] += c;
-                    rr[1] = fmaf(c, y, rr[1]);
-                    const float y2 = y * y;
-                    rr[2] = fmaf(c, y2, rr[2]);
-                    rr[3] = fmaf(c, y2 * y, rr[3]);
-                }
+                const bool itm = ((valid >> i) & 1u) && h > 0.f;
+                const float c = itm ? cf[i] : 0.f;
+                const float y = itm ? fmaf(s, invK, -1.f) : 0.f;
+                const float y2 = y * y;
+                rr[0] += c;
+                rr[1] = fmaf(c, y, rr[1]);
+                rr[2] = fmaf(c, y2, rr[2]);
+                rr[3] = fmaf(c, y2 * y, rr[3]);
             }
             if (j + 1 <= m - 1 && sm.deg_cur && w == 0) ++degenerate;
 #pragma unroll
