@@ -276,8 +276,11 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         items.push_back(it);
     }
     // group by (plan kind, chunks, rule class), keeping input order within a group
-    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+    // (the mixed LSM kernel is also specialised on put / call)
+    auto tkey = [&](const Item &it) { return it.pl.kind == 2 ? opts[it.idx].type : 0; };
+    std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
         if (a.pl.kind != b.pl.kind) return a.pl.kind < b.pl.kind;
+        if (tkey(a) != tkey(b)) return tkey(a) < tkey(b);
         if (a.pl.chunks != b.pl.chunks) return a.pl.chunks < b.pl.chunks;
         return a.lsm && !b.lsm;
     });
@@ -296,8 +299,9 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         size_t bytes = 0;
         int ctas = 0, max_m = 1;
         size_t budget = c->arena_bytes;
+        const int type0 = tkey(items[pos]);
         while (pos < items.size() && items[pos].pl.kind == plan0.kind && items[pos].pl.chunks == chunks &&
-               items[pos].lsm == lsm) {
+               items[pos].lsm == lsm && tkey(items[pos]) == type0) {
             const amc_option &o = opts[items[pos].idx];
             size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);
             need += align_up((size_t)o.n_steps * items[pos].pl.ctas * kNV * 8, 256);   // partials
@@ -379,6 +383,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         a.n_jobs = nw;
         a.max_m = max_m;
         a.max_slots = max_slots;
+        a.jobs_type = opts[wave[0].idx].type;
         a.total = tiles;
         a.V = c->V;
         AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));

@@ -184,7 +184,44 @@ __device__ __forceinline__ double gram_inverse(const double *M, int p, int lane,
     return (k < p && l < p) ? cof * rd * sP[k] * sP[l] : 0.0;
 }
 
-template <bool GREEKS>
+// Warp sums by transposition: 8 values (7 used) over 32 lanes in 5 exchange
+// steps; lane l ends with the full sum of value (l >> 2) & 7.  Fixed
+// pattern, so the result does not depend on timing.
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float u[4], t[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[k + 4];
+        u[k] = (b4 ? v[k + 4] : v[k]) + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? u[k] : u[k + 2];
+        t[k] = (b3 ? u[k + 2] : u[k]) + __shfl_xor_sync(kFull, send, 8);
+    }
+    float r = (b2 ? t[1] : t[0]) + __shfl_xor_sync(kFull, b2 ? t[0] : t[1], 4);
+    r += __shfl_xor_sync(kFull, r, 2);
+    r += __shfl_xor_sync(kFull, r, 1);
+    return r;
+}
+// Same for 4 values: lane l ends with the sum of value (l >> 3) & 3.
+__device__ __forceinline__ float warp_sum4(const float (&v)[4], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float u[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b4 ? v[k] : v[k + 2];
+        u[k] = (b4 ? v[k + 2] : v[k]) + __shfl_xor_sync(kFull, send, 16);
+    }
+    float r = (b3 ? u[1] : u[0]) + __shfl_xor_sync(kFull, b3 ? u[0] : u[1], 8);
+    r += __shfl_xor_sync(kFull, r, 4);
+    r += __shfl_xor_sync(kFull, r, 2);
+    r += __shfl_xor_sync(kFull, r, 1);
+    return r;
+}
+
+template <bool GREEKS, bool PUT>
 __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_constant__ KArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemV2 &sm = *reinterpret_cast<SmemV2 *>(smem_raw);
@@ -193,8 +230,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lc = blockIdx.x - J.cta_begin, G = J.n_cta;
     const int m = J.m, p = J.p, nmom = 2 * p - 1;
-    const bool put = J.type == AMC_PUT;
-    const float K = (float)J.K, invK = (float)J.invK, disc = (float)J.disc;
+    const float invK = (float)J.invK, disc = (float)J.disc;
     const float *__restrict__ S = reinterpret_cast<const float *>(J.S);
     const int64_t N = J.N, ld = J.ld;
     const int64_t base = (int64_t)lc * kPPC;
@@ -231,7 +267,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                     bail = true;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(64);
             }
             bail = __any_sync(kFull, bail);
             if (bail) {
@@ -255,6 +291,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     }
 
     // ------------------------------------------------------------ path warps
+    // Per-path state is held in units of K: cash flow cf, and for Greeks the
+    // stopping date and y = S/K - 1 at stopping.  The ring slots hold S as
+    // copied from HBM until the Gram pass of that date rewrites them in place
+    // as y for in-the-money own paths and 0 otherwise; later passes then need
+    // no payoff, moneyness or validity arithmetic (ITM <=> y != 0).
     const int w = tid - 32;
     auto issue = [&](int d) {            // w == 0 only
         const int s = d % kSlots;
@@ -277,44 +318,37 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if (w == 0) sm.pend[s] = 0;
         return true;
     };
-    // validity of the own paths (ragged last CTA), fixed for the whole sweep
-    uint32_t valid = 0;
+    uint32_t valid = 0;                  // own paths below N (ragged last CTA)
 #pragma unroll
     for (int i = 0; i < kPPT; ++i)
         if (base + w + i * kWorkers < N) valid |= 1u << i;
-    // in-the-money Gram moments of date d over the own paths, summed over
-    // the warp and left in sm.redG[buf][warp][k] for a later exchange
+    // Gram pass of date d: y in place, in-the-money moments summed over the
+    // warp into sm.redG[buf][warp][k]
     auto gram_post = [&](int d, int buf) {
-        float g[7];
+        float g[8];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) g[k] = 0.f;
-        const float *sl = sm.S[d % kSlots];
+        for (int k = 0; k < 8; ++k) g[k] = 0.f;
+        float *sl = sm.S[d % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
             const float s = sl[w + i * kWorkers];
-            const float h = payoff(put, s, K);
-            // branch-free: weight 1 for in-the-money own paths, 0 otherwise;
-            // y is selected (not multiplied) to 0 so stale slots never reach a sum
-            const bool itm = ((valid >> i) & 1u) && h > 0.f;
-            const float one = itm ? 1.f : 0.f;
-            const float y = itm ? fmaf(s, invK, -1.f) : 0.f;
+            const float yr = fmaf(s, invK, -1.f);
+            const bool itm = ((valid >> i) & 1u) && (PUT ? yr < 0.f : yr > 0.f);
+            const float y = itm ? yr : 0.f;
+            sl[w + i * kWorkers] = y;
             const float y2 = y * y, y3 = y2 * y;
-            g[0] += one;
-            g[1] = fmaf(one, y, g[1]);
-            g[2] = fmaf(one, y2, g[2]);
-            g[3] = fmaf(one, y3, g[3]);
-            g[4] = fmaf(one, y2 * y2, g[4]);
-            g[5] = fmaf(one, y2 * y3, g[5]);
-            g[6] = fmaf(one, y3 * y3, g[6]);
+            g[0] += itm ? 1.f : 0.f;
+            g[1] += y;
+            g[2] += y2;
+            g[3] += y3;
+            g[4] = fmaf(y2, y2, g[4]);
+            g[5] = fmaf(y2, y3, g[5]);
+            g[6] = fmaf(y3, y3, g[6]);
         }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            if (k < nmom) {
-#pragma unroll
-                for (int off = 16; off; off >>= 1) g[k] += __shfl_xor_sync(kFull, g[k], off);
-                if (lane == 0) sm.redG[buf][warp][k] = g[k];
-            }
-        }
+        fence_proxy_async();             // these generic writes precede a later TMA refill
+        const float r = warp_sum8(g, lane);
+        const int k = (lane >> 2) & 7;
+        if ((lane & 3) == 0 && k < nmom) sm.redG[buf][warp][k] = r;
     };
 
     if (w == 0)
@@ -322,16 +356,17 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
 
     float cf[kPPT];
     int tau[GREEKS ? kPPT : 1];
-    float st[GREEKS ? kPPT : 1];
+    float yt[GREEKS ? kPPT : 1];
     int degenerate = 0;
     const bool ok = wait_slice(m);
     if (ok) {
         const float *sl = sm.S[m % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
-            const float s = sl[w + i * kWorkers];
-            cf[i] = ((valid >> i) & 1u) ? payoff(put, s, K) : 0.f;
-            if (GREEKS) { tau[i] = m; st[i] = s; }
+            const float y = fmaf(sl[w + i * kWorkers], invK, -1.f);
+            const float h = PUT ? -y : y;
+            cf[i] = (((valid >> i) & 1u) && h > 0.f) ? h : 0.f;
+            if (GREEKS) { tau[i] = m; yt[i] = y; }
         }
     }
     bool stop = bar_work_any(!ok || sm.abort);
@@ -339,65 +374,58 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // Gram moments of date m-1, posted at the first exchange (index m+1)
     if (m >= 2 && !stop && wait_slice(m - 1)) gram_post(m - 1, (m + 1) & 1);
 
-    // exercise at date d with the coefficients in sm.beta (fused into the
-    // right-hand-side pass of the next date)
-    auto exercise = [&](int d, int i, float b0, float b1, float b2, float b3) {
-        const float s = sm.S[d % kSlots][w + i * kWorkers];
-        const float h = payoff(put, s, K);
-        const float y = fmaf(s, invK, -1.f);
-        const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
-        const bool ex = ((valid >> i) & 1u) && h > 0.f && h > cont;
-        cf[i] = ex ? h : cf[i];
-        if (GREEKS) {
-            tau[i] = ex ? d : tau[i];
-            st[i] = ex ? s : st[i];
+    // exercise at date d with the coefficients in sm.beta
+    auto exercise = [&](int d, float b0, float b1, float b2, float b3) {
+        const float *sl = sm.S[d % kSlots];
+#pragma unroll
+        for (int i = 0; i < kPPT; ++i) {
+            const float y = sl[w + i * kWorkers];
+            const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+            const float h = PUT ? -y : y;
+            const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
+            cf[i] = ex ? h : cf[i];
+            if (GREEKS) {
+                tau[i] = ex ? d : tau[i];
+                yt[i] = ex ? y : yt[i];
+            }
         }
     };
 
     for (int j = m + 1; j >= 1 && !stop; --j) {
         const bool hasR = j <= m - 1;
         const bool hasG = j - 2 >= 1;
-        float rr[4] = {0.f, 0.f, 0.f, 0.f};
         if (hasR) {
             // exercise at j+1 (coefficients of the previous exchange), then
             // discount to t_j and sum the right-hand sides of date j
-            const bool ex = j + 1 <= m - 1 && !sm.deg_cur;
-            const float b0 = (float)sm.beta[0], b1 = (float)sm.beta[1];
-            const float b2 = (float)sm.beta[2], b3 = (float)sm.beta[3];
-            const float *sl = sm.S[j % kSlots];
-            if (ex) {                                             // uniform: keep the loop body branch-free
-#pragma unroll
-                for (int i = 0; i < kPPT; ++i) exercise(j + 1, i, b0, b1, b2, b3);
+            if (j + 1 <= m - 1) {
+                if (sm.deg_cur) {
+                    if (w == 0) ++degenerate;
+                } else {
+                    exercise(j + 1, (float)sm.beta[0], (float)sm.beta[1], (float)sm.beta[2], (float)sm.beta[3]);
+                }
             }
+            float rr[4] = {0.f, 0.f, 0.f, 0.f};
+            const float *sl = sm.S[j % kSlots];
 #pragma unroll
             for (int i = 0; i < kPPT; ++i) {
                 cf[i] *= disc;
-                const float s = sl[w + i * kWorkers];
-                const float h = payoff(put, s, K);
-                const bool itm = ((valid >> i) & 1u) && h > 0.f;
-                const float c = itm ? cf[i] : 0.f;
-                const float y = itm ? fmaf(s, invK, -1.f) : 0.f;
+                const float y = sl[w + i * kWorkers];
+                const float c = y != 0.f ? cf[i] : 0.f;
                 const float y2 = y * y;
                 rr[0] += c;
                 rr[1] = fmaf(c, y, rr[1]);
                 rr[2] = fmaf(c, y2, rr[2]);
                 rr[3] = fmaf(c, y2 * y, rr[3]);
             }
-            if (j + 1 <= m - 1 && sm.deg_cur && w == 0) ++degenerate;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (k < p) {
-#pragma unroll
-                    for (int off = 16; off; off >>= 1) rr[k] += __shfl_xor_sync(kFull, rr[k], off);
-                    if (lane == 0) sm.redR[warp][k] = rr[k];
-                }
-            }
+            const float r = warp_sum4(rr, lane);
+            const int k = (lane >> 3) & 3;
+            if ((lane & 7) == 0 && k < p) sm.redR[warp][k] = r;
         }
         const uint32_t mask = (hasG ? ((1u << nmom) - 1u) : 0u) | (hasR ? (((1u << p) - 1u) << 7) : 0u);
         bar_work();                                               // B1
         if (w == 0 && j + 1 <= m - 1 && j + 1 - kSlots >= 1) issue(j + 1 - kSlots);   // slice j+1 consumed
         // cross-CTA exchange: warp 1+k owns value slot k; it posts first, then
-        // computes its share of the next Gram moments, then gathers
+        // does its share of the next Gram pass, then gathers
         const uint32_t tag = tag_hi | (uint32_t)j;
         const bool xw = warp >= 1 && warp <= kXV && ((mask >> (warp - 1)) & 1u);
         const int xk = warp - 1;
@@ -408,7 +436,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             if (lane == 0 && inject_date != j)
                 st_unit(xu + lc, ((uint64_t)tag << 32) | __float_as_uint(__fadd_rn(part.hi, part.lo)));
         }
-        // Gram moments of date j-3, posted at the next exchange
+        // Gram pass of date j-3, posted at the next exchange
         if (j - 3 >= 1 && !sm.abort && wait_slice(j - 3)) gram_post(j - 3, (j - 1) & 1);
         if (xw) {
             float vals[kMaxCtas / 32];
@@ -482,10 +510,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if (sm.deg_cur) {
             if (w == 0) ++degenerate;
         } else {
-            const float b0 = (float)sm.beta[0], b1 = (float)sm.beta[1];
-            const float b2 = (float)sm.beta[2], b3 = (float)sm.beta[3];
-#pragma unroll
-            for (int i = 0; i < kPPT; ++i) exercise(1, i, b0, b1, b2, b3);
+            exercise(1, (float)sm.beta[0], (float)sm.beta[1], (float)sm.beta[2], (float)sm.beta[3]);
         }
     }
 
@@ -504,37 +529,40 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         return;
     }
 
-    // final per-CTA sums: CF, CF^2, delta, vega (discounting to 0 in finalize)
+    // final per-CTA sums (units of K): CF, CF^2, delta, vega; discounting to
+    // 0 happens in finalize
     float fs[4] = {0.f, 0.f, 0.f, 0.f};
+    const float Kf = (float)J.K;
     const float S0 = (float)J.S0, r = (float)J.r, sig = (float)J.sigma, dt = (float)J.dt;
     const float mu = r - 0.5f * sig * sig;
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
-        const int li = w + i * kWorkers;
-        if (base + li >= N) continue;
+        if (!((valid >> i) & 1u)) continue;
         fs[0] += cf[i];
         fs[1] += cf[i] * cf[i];
         if (GREEKS && cf[i] > 0.f) {
+            const float St = Kf * (1.f + yt[i]);
             const float t = (float)tau[i] * dt;
             const float dfac = expf(-r * t);
-            const float dh = put ? -1.f : 1.f;
-            const float Wt = (logf(st[i] / S0) - mu * t) / sig;
-            fs[2] += dfac * dh * st[i] / S0;
-            fs[3] += dfac * dh * st[i] * (Wt - sig * t);
+            const float dh = PUT ? -1.f : 1.f;
+            const float Wt = (logf(St / S0) - mu * t) / sig;
+            fs[2] += dfac * dh * St / S0;
+            fs[3] += dfac * dh * St * (Wt - sig * t);
         }
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int off = 16; off; off >>= 1) fs[k] += __shfl_xor_sync(kFull, fs[k], off);
-        if (lane == 0) sm.red[warp][k] = fs[k];
+    {
+        const float rsum = warp_sum4(fs, lane);
+        const int k = (lane >> 3) & 3;
+        if ((lane & 7) == 0) sm.red[warp][k] = rsum;
     }
     bar_work();
     if (warp >= 1 && warp <= 4) {
         const int k = warp - 1;
         dfl part = {lane < 31 ? sm.red[lane + 1][k] : 0.f, 0.f};
         part = df_warp_sum(part);
-        if (lane == 0) reinterpret_cast<double *>(J.fin)[(int64_t)lc * 4 + k] = (double)part.hi + (double)part.lo;
+        const double scale = k == 0 ? J.K : (k == 1 ? J.K * J.K : 1.0);
+        if (lane == 0)
+            reinterpret_cast<double *>(J.fin)[(int64_t)lc * 4 + k] = scale * ((double)part.hi + (double)part.lo);
     }
     if (lc == 0 && w == 0) J.res[4] = (double)degenerate;
 }
@@ -542,7 +570,9 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
 }  // namespace
 
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st) {
-    const void *f = greeks ? (const void *)sweep_lsm_v2_kernel<true> : (const void *)sweep_lsm_v2_kernel<false>;
+    const bool put = (a.jobs ? a.jobs_type : a.one.type) == AMC_PUT;
+    const void *f = greeks ? (put ? (const void *)sweep_lsm_v2_kernel<true, true> : (const void *)sweep_lsm_v2_kernel<true, false>)
+                           : (put ? (const void *)sweep_lsm_v2_kernel<false, true> : (const void *)sweep_lsm_v2_kernel<false, false>);
     const int smem = (int)sizeof(SmemV2);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
