@@ -124,6 +124,46 @@ def cpu_baseline(opt, n_sample=2 ** 16):
                 n_sample, opt.n_paths, opt.n_steps, dt)}
 
 
+def serve_replay(amc, ctx, times, opts, slots=3, max_batch=128, prec=1):
+    """Replay arrivals (seconds from start) through the serving loop.
+    Returns latency percentiles, throughput and counts."""
+    amc.amc_serve_start(ctx, slots=slots, max_batch=max_batch, prec=prec)
+    lat, steps, bad = [], 0, 0
+    outstanding = 0
+    t0 = time.perf_counter()
+    last_drain = 0.0
+
+    def drain():
+        nonlocal outstanding, steps, bad
+        for _, r, l in amc.amc_serve_drain(ctx):
+            outstanding -= 1
+            lat.append(l)
+            bad += r["status"] != 0
+    for t, o in zip(times, opts):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= t:
+                break
+            if now - last_drain > 0.001:
+                drain()
+                last_drain = now
+            time.sleep(min(0.0002, t - now))
+        amc.amc_serve_submit(ctx, o)
+        outstanding += 1
+        steps += o.n_paths * o.n_steps
+    while outstanding > 0:
+        drain()
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    stats = amc.amc_serve_stats_get(ctx)
+    amc.amc_serve_stop(ctx)
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3
+    return {"requests": len(lat), "offered_per_s": len(times) / max(times[-1], 1e-9), "wall_s": wall,
+            "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat[-1] * 1e3, "failed": bad,
+            "path_steps_per_s": steps / wall, "batches": stats["batches"], "slots": slots}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -287,6 +327,15 @@ def run_amc(args):
             "gpu_launches": 3 * args.steps,
             "roofline": dominant, "roofline_sweep": rl_sweep, "roofline_pathgen": rl_gen,
             "clocks": ck}
+    if args.serve_seconds > 0:
+        times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
+        sctx = amc.Context(local, arena_bytes=24 << 30)
+        # warm the tables and kernels for every date count the replay will see
+        sv = serve_replay(amc, sctx, [0.0] * 8, sopts[:8])
+        sv = serve_replay(amc, sctx, list(times), sopts)
+        sv["workload"] = "Poisson 2000 req/s, %.0f s of the seed-4 request stream" % args.serve_seconds
+        line["serving"] = sv
+        sctx.close()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(opt)
     print(json.dumps(line), flush=True)
@@ -305,6 +354,8 @@ def main():
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.profile:
         args.warmup = 3

@@ -169,6 +169,39 @@ int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
 int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                double *price, double *delta, double *vega);
 
+/* ------------------------------------------------------------ serving */
+/* Continuous batching of pricing requests (the paper's many-options
+ * motivation, §III.D).  While serving runs, the context belongs to its
+ * scheduler thread: the other pricing calls on it return AMC_EBUSY.        */
+typedef struct amc_serve_config {
+    size_t slot_bytes;   /* device memory per slot (0: arena / slots)       */
+    int32_t slots;       /* concurrent batches on the GPU, 1..8             */
+    int32_t max_batch;   /* requests per batch, 1..4096                     */
+    int32_t max_pending; /* queue bound; submits beyond it get AMC_EBUSY    */
+    int32_t prec;        /* AMC_MIXED or AMC_FP64                           */
+} amc_serve_config;
+
+typedef struct amc_serve_stats {
+    int64_t submitted, launched, completed, rejected, batches, pending;
+} amc_serve_stats;
+
+/* Start the scheduler thread.  Admission is by memory footprint: a request
+ * whose paths and scratch exceed one slot is refused at submit (AMC_EBUSY);
+ * otherwise it waits until a slot with room is free.  The oldest pending
+ * request fixes the launch group of the next batch.                        */
+int amc_serve_start(amc_ctx *ctx, const amc_serve_config *cfg);
+/* Queue one request (thread-safe, non-blocking); *ticket identifies it.    */
+int amc_serve_submit(amc_ctx *ctx, const amc_option *opt, uint64_t *ticket);
+/* AMC_PENDING until done; then the result and the latency from submit to
+ * completion (seconds), and the ticket is released.  Thread-safe.          */
+int amc_serve_poll(amc_ctx *ctx, uint64_t ticket, amc_result *out, double *latency_s);
+/* Up to `cap` finished requests, released; *n_out of them.  Thread-safe.   */
+int amc_serve_drain(amc_ctx *ctx, uint64_t *tickets, amc_result *out, double *latency_s, int cap,
+                    int *n_out);
+int amc_serve_stats_get(amc_ctx *ctx, amc_serve_stats *out);
+/* Finish every queued request, then stop the scheduler.                    */
+int amc_serve_stop(amc_ctx *ctx);
+
 /* ------------------------------------------- allocation-free sweep */
 /* Step 4 (as amc_sweep) without a context and without allocating device
  * memory.  The paper has no counterpart: this entry point exists for

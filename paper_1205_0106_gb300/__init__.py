@@ -38,6 +38,16 @@ class amc_result(ctypes.Structure):
                 ("ms_gen", ctypes.c_float), ("ms_sweep", ctypes.c_float)]
 
 
+class amc_serve_config(ctypes.Structure):
+    _fields_ = [("slot_bytes", ctypes.c_size_t), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class amc_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("launched", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64), ("pending", ctypes.c_int64)]
+
+
 class AmcError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -79,6 +89,12 @@ SIGNATURES = {
                                           ctypes.c_int, ctypes.c_int, _resp]),
     "amc_price_batch": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _resp]),
     "amc_greeks": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "amc_serve_start": (ctypes.c_int, [_vp, ctypes.POINTER(amc_serve_config)]),
+    "amc_serve_submit": (ctypes.c_int, [_vp, _optp, ctypes.POINTER(_u64)]),
+    "amc_serve_poll": (ctypes.c_int, [_vp, _u64, _resp, _dp]),
+    "amc_serve_drain": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _resp, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "amc_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(amc_serve_stats)]),
+    "amc_serve_stop": (ctypes.c_int, [_vp]),
     "amc_sweep_noalloc": (ctypes.c_int, [_optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "amc_sweep_noalloc_capacity": (ctypes.c_size_t, []),
 }
@@ -254,6 +270,49 @@ def amc_price_device(ctx, opt, prec, S, res, ld=None, stream=None):
     ld = S.shape[1] if ld is None else ld
     _check(lib().amc_price_device(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(res),
                                   _stream(stream)), "amc_price_device")
+
+
+# ------------------------------------------------------------ serving
+def amc_serve_start(ctx, slots=2, max_batch=256, max_pending=1 << 20, prec=AMC_MIXED, slot_bytes=0):
+    cfg = amc_serve_config(slot_bytes, slots, max_batch, max_pending, prec)
+    _check(lib().amc_serve_start(ctx.handle, ctypes.byref(cfg)), "amc_serve_start")
+
+
+def amc_serve_submit(ctx, opt):
+    """Queue one request; returns its ticket (raises AmcError, e.g. AMC_EBUSY)."""
+    t = _u64()
+    _check(lib().amc_serve_submit(ctx.handle, ctypes.byref(make_option(opt)), ctypes.byref(t)), "amc_serve_submit")
+    return t.value
+
+
+def amc_serve_poll(ctx, ticket):
+    """None while pending, else (result dict, latency seconds)."""
+    r, lat = amc_result(), ctypes.c_double()
+    rc = lib().amc_serve_poll(ctx.handle, ticket, ctypes.byref(r), ctypes.byref(lat))
+    if rc == AMC_PENDING:
+        return None
+    _check(rc, "amc_serve_poll")
+    return _res_dict(r), lat.value
+
+
+def amc_serve_drain(ctx, cap=4096):
+    """Finished requests: list of (ticket, result dict, latency seconds)."""
+    tk = (_u64 * cap)()
+    rs = (amc_result * cap)()
+    lat = (ctypes.c_double * cap)()
+    n = ctypes.c_int()
+    _check(lib().amc_serve_drain(ctx.handle, tk, rs, lat, cap, ctypes.byref(n)), "amc_serve_drain")
+    return [(tk[i], _res_dict(rs[i]), lat[i]) for i in range(n.value)]
+
+
+def amc_serve_stats_get(ctx):
+    st = amc_serve_stats()
+    _check(lib().amc_serve_stats_get(ctx.handle, ctypes.byref(st)), "amc_serve_stats_get")
+    return {f: getattr(st, f) for f, _ in amc_serve_stats._fields_}
+
+
+def amc_serve_stop(ctx):
+    _check(lib().amc_serve_stop(ctx.handle), "amc_serve_stop")
 
 
 def amc_sweep_noalloc(opt, prec, S, res, ld=None, with_greeks=False, stream=None):

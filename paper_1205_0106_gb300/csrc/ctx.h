@@ -1,0 +1,95 @@
+// The amc_ctx structure and the batch-launch helpers shared by the C-ABI
+// runtime (runtime.cu) and the serving loop (serve.cpp).  Internal.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace amc {
+
+struct DevBridge {
+    NodeF *nf = nullptr;
+    NodeD *nd = nullptr;
+    int nslots = 0;
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over a fixed region of device memory.
+struct SubArena {
+    char *base = nullptr;
+    size_t size = 0, top = 0;
+    int alloc(size_t bytes, void **p) {
+        const size_t off = align_up(top, 256);
+        if (off + bytes > size) return AMC_ENOMEM;
+        *p = base + off;
+        top = off + bytes;
+        return AMC_OK;
+    }
+};
+
+struct Server;   // serve.cpp
+
+}  // namespace amc
+
+struct amc_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    // path arena (bump allocation, reset by each host-level call)
+    char *arena = nullptr;
+    size_t arena_bytes = 0, arena_top = 0;
+    // tables
+    uint32_t *V = nullptr;                           // [AMC_MAX_STEPS][32]
+    std::unordered_map<int, amc::DevBridge> bridges;  // by n_steps
+    // single-option scratch (step-level calls); the job itself travels by
+    // value in the kernel arguments
+    amc::KArgs args;
+    uint32_t *shift1 = nullptr;
+    void *part1 = nullptr;
+    uint32_t *arrive1 = nullptr;
+    double *fin1 = nullptr;
+    double *res1 = nullptr;
+    int32_t *status1 = nullptr;
+    uint64_t *xch1 = nullptr;                        // exchange units of the mixed LSM sweep
+    uint32_t epoch = 0;                              // launch tag of those units
+    int gcap = 0;
+    double *res_host = nullptr;                      // pinned
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    double timeout_s = 2.0;
+    int inject_kind = 0;
+    int64_t inject_arg = 0;
+    std::mutex mu;                                   // launches and tables
+    amc::Server *server = nullptr;                   // running serving loop, if any
+};
+
+namespace amc {
+
+// Options that can share one launch have the same group key.
+struct GroupKey {
+    int kind, type, chunks;
+    bool lsm;
+    bool operator==(const GroupKey &o) const {
+        return kind == o.kind && type == o.type && chunks == o.chunks && lsm == o.lsm;
+    }
+};
+GroupKey group_key(const amc_option &o, const SweepPlan &pl);
+// CTAs one launch of this group may use (co-resident capacity).
+int group_cta_cap(amc_ctx *c, const SweepPlan &pl);
+// Device bytes one option of a group needs (paths and sweep scratch).
+size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec);
+// Launch path generation, sweep and finalize for n options of one group on
+// stream st, memory from ar; results (AMC_RES_DOUBLES per option, input
+// order) in *res_dev.  Asynchronous.  Caller holds c->mu.
+int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int n, int prec, bool greeks,
+                 SubArena &ar, cudaStream_t st, double **res_dev);
+int result_from(const double *r, amc_result *out);
+
+}  // namespace amc

@@ -15,47 +15,7 @@
 
 using namespace amc;
 
-namespace {
-
-struct DevBridge {
-    NodeF *nf = nullptr;
-    NodeD *nd = nullptr;
-    int nslots = 0;
-};
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-}  // namespace
-
-struct amc_ctx {
-    int device = 0;
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    // path arena (bump allocation, reset by each host-level call)
-    char *arena = nullptr;
-    size_t arena_bytes = 0, arena_top = 0;
-    // tables
-    uint32_t *V = nullptr;                      // [AMC_MAX_STEPS][32]
-    std::unordered_map<int, DevBridge> bridges;  // by n_steps
-    // single-option scratch (step-level calls); the job itself travels by
-    // value in the kernel arguments
-    KArgs args;
-    uint32_t *shift1 = nullptr;
-    void *part1 = nullptr;
-    uint32_t *arrive1 = nullptr;
-    double *fin1 = nullptr;
-    double *res1 = nullptr;
-    int32_t *status1 = nullptr;
-    uint64_t *xch1 = nullptr;                   // exchange units of the mixed LSM sweep
-    uint32_t epoch = 0;                         // launch tag of those units
-    int gcap = 0;
-    double *res_host = nullptr;                 // pinned
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    double timeout_s = 2.0;
-    int inject_kind = 0;
-    int64_t inject_arg = 0;
-    std::mutex mu;
-};
+#include "ctx.h"
 
 namespace {
 
@@ -229,16 +189,6 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     return launch_sweeps(c, a, pl, pl.ctas, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st);
 }
 
-int result_from(const double *r, amc_result *out) {
-    memset(out, 0, sizeof(*out));
-    out->price = r[0];
-    out->std_err = r[1];
-    out->delta = r[2];
-    out->vega = r[3];
-    out->degenerate_dates = (int32_t)r[4];
-    out->status = (int32_t)r[5];
-    return out->status;
-}
 
 amc_option make_option(double S0, double K, double r, double sigma, double T, int n_steps, int64_t n_paths,
                        int basis, int type, uint64_t seed, int rule) {
@@ -252,149 +202,74 @@ amc_option make_option(double S0, double K, double r, double sigma, double T, in
 
 // ------------------------------------------------------------- batches
 // A wave: options whose paths fit the arena and whose sweep CTAs fit one
-// co-resident launch; within a wave the options share the chunk count, the
-// rule class and the precision.
+// co-resident launch; within a wave the options share the group key
+// (plan kind, put/call for the mixed LSM kernel, chunk count, rule class).
 int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, amc_result *out) {
     AMC_TRY(check_prec(prec));
     for (int i = 0; i < n; ++i) {
         AMC_TRY(host_validate(&opts[i]));
         if (greeks && opts[i].rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
     }
-    const bool fp64 = prec == AMC_FP64;
-    const size_t esz = fp64 ? 8 : 4;
     struct Item {
         int idx;
         SweepPlan pl;
-        bool lsm;
+        GroupKey key;
     };
     std::vector<Item> items;
     for (int i = 0; i < n; ++i) {
         Item it;
         it.idx = i;
         AMC_TRY(host_plan_sweep(opts[i].n_paths, c->sm_count, prec, opts[i].rule, &it.pl));
-        it.lsm = opts[i].rule == AMC_RULE_LSM;
+        it.key = group_key(opts[i], it.pl);
         items.push_back(it);
     }
-    // group by (plan kind, chunks, rule class), keeping input order within a group
-    // (the mixed LSM kernel is also specialised on put / call)
-    auto tkey = [&](const Item &it) { return it.pl.kind == 2 ? opts[it.idx].type : 0; };
+    // group by key, keeping input order within a group
     std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
-        if (a.pl.kind != b.pl.kind) return a.pl.kind < b.pl.kind;
-        if (tkey(a) != tkey(b)) return tkey(a) < tkey(b);
-        if (a.pl.chunks != b.pl.chunks) return a.pl.chunks < b.pl.chunks;
-        return a.lsm && !b.lsm;
+        if (a.key.kind != b.key.kind) return a.key.kind < b.key.kind;
+        if (a.key.type != b.key.type) return a.key.type < b.key.type;
+        if (a.key.chunks != b.key.chunks) return a.key.chunks < b.key.chunks;
+        return a.key.lsm && !b.key.lsm;
     });
     for (int i = 0; i < n; ++i) memset(&out[i], 0, sizeof(amc_result));
     size_t pos = 0;
     cudaStream_t st = c->stream;
+    SubArena ar;
+    ar.base = c->arena;
+    ar.size = c->arena_bytes;
     while (pos < items.size()) {
-        const SweepPlan plan0 = items[pos].pl;
-        const int chunks = plan0.chunks;
-        const bool lsm = items[pos].lsm;
-        const int cap = plan0.kind == 2 ? std::min(c->sm_count, kV2MaxCtas)
-                                        : sweep_ctas_per_sm(chunks) * c->sm_count;
-        c->arena_top = 0;
-        // per-wave fixed scratch sized for the worst case of this wave
-        std::vector<Item> wave;
-        size_t bytes = 0;
-        int ctas = 0, max_m = 1;
-        size_t budget = c->arena_bytes;
-        const int type0 = tkey(items[pos]);
-        while (pos < items.size() && items[pos].pl.kind == plan0.kind && items[pos].pl.chunks == chunks &&
-               items[pos].lsm == lsm && tkey(items[pos]) == type0) {
+        const GroupKey key = items[pos].key;
+        const int cap = group_cta_cap(c, items[pos].pl);
+        std::vector<const amc_option *> wopts;
+        std::vector<SweepPlan> wplans;
+        std::vector<int> widx;
+        size_t bytes = 4096;
+        int ctas = 0;
+        while (pos < items.size() && items[pos].key == key) {
             const amc_option &o = opts[items[pos].idx];
-            size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);
-            need += align_up((size_t)o.n_steps * items[pos].pl.ctas * kNV * 8, 256);   // partials
-            need += align_up(v2_xch_units(o.n_steps, items[pos].pl.ctas) * 8, 256);    // exchange units
-            need += align_up((size_t)o.n_steps * 4, 256) * 2;                          // arrive + shifts
-            need += align_up((size_t)items[pos].pl.ctas * 32, 256) + 256 + sizeof(Job) + 256;
-            if (!wave.empty() && (bytes + need > budget || ctas + items[pos].pl.ctas > cap)) break;
-            if (need > budget) return AMC_ENOMEM;
-            wave.push_back(items[pos]);
+            const size_t need = option_bytes(o, items[pos].pl, prec);
+            if (!wopts.empty() && (bytes + need > ar.size || ctas + items[pos].pl.ctas > cap)) break;
+            if (bytes + need > ar.size) return AMC_ENOMEM;
+            wopts.push_back(&o);
+            wplans.push_back(items[pos].pl);
+            widx.push_back(items[pos].idx);
             bytes += need;
             ctas += items[pos].pl.ctas;
-            max_m = std::max(max_m, o.n_steps);
             ++pos;
         }
-        const int nw = (int)wave.size();
-        std::vector<Job> jobs(nw);
-        Job *jobs_dev;
-        int32_t *status_dev;
-        double *res_dev;
-        uint32_t *arrive_all;
-        AMC_TRY(arena_alloc(c, sizeof(Job) * nw, (void **)&jobs_dev));
-        AMC_TRY(arena_alloc(c, sizeof(int32_t), (void **)&status_dev));
-        AMC_TRY(arena_alloc(c, sizeof(double) * AMC_RES_DOUBLES * nw, (void **)&res_dev));
-        size_t arrive_words = 0;
-        for (auto &it : wave) arrive_words += opts[it.idx].n_steps;
-        AMC_TRY(arena_alloc(c, sizeof(uint32_t) * arrive_words, (void **)&arrive_all));
-        std::vector<uint32_t> shifts;
-        std::vector<size_t> shift_off(nw);
-        for (int k = 0; k < nw; ++k) {
-            const amc_option &o = opts[wave[k].idx];
-            shift_off[k] = shifts.size();
-            shifts.resize(shifts.size() + o.n_steps);
-            host_shifts(o.seed, o.n_steps, shifts.data() + shift_off[k]);
+        if (c->inject_kind == 2) {
+            c->inject_kind = 0;
+            return AMC_ENOMEM;
         }
-        uint32_t *shift_dev;
-        AMC_TRY(arena_alloc(c, sizeof(uint32_t) * shifts.size(), (void **)&shift_dev));
-        int64_t tiles = 0;
-        int cta = 0, max_slots = 1;
-        size_t arr_off = 0;
-        for (int k = 0; k < nw; ++k) {
-            const amc_option &o = opts[wave[k].idx];
-            Job &J = jobs[k];
-            fill_job_common(&o, &J);
-            DevBridge *b;
-            AMC_TRY(get_bridge(c, o.n_steps, &b));
-            J.shift = shift_dev + shift_off[k];
-            J.nodes = fp64 ? (const void *)b->nd : (const void *)b->nf;
-            J.nslots = b->nslots;
-            max_slots = std::max(max_slots, b->nslots);
-            J.ld = host_ld(o.n_paths);
-            AMC_TRY(arena_alloc(c, (size_t)o.n_steps * J.ld * esz, &J.S));
-            J.tile_begin = tiles;
-            J.n_tiles = (o.n_paths + kTilePoints - 1) / kTilePoints;
-            tiles += J.n_tiles;
-            J.cta_begin = cta;
-            J.n_cta = wave[k].pl.ctas;
-            J.chunks = chunks;
-            cta += J.n_cta;
-            J.greeks = greeks ? 1 : 0;
-            if (plan0.kind == 2) {
-                AMC_TRY(arena_alloc(c, v2_xch_units(o.n_steps, J.n_cta) * 8, (void **)&J.xch));
-            } else {
-                AMC_TRY(arena_alloc(c, (size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
-            }
-            J.arrive = arrive_all + arr_off;
-            arr_off += o.n_steps;
-            AMC_TRY(arena_alloc(c, (size_t)J.n_cta * 4 * sizeof(double), &J.fin));
-            J.res = res_dev + (size_t)k * AMC_RES_DOUBLES;
-            J.status = status_dev;
-        }
-        AMC_TRY_CUDA(cudaMemcpyAsync(shift_dev, shifts.data(), sizeof(uint32_t) * shifts.size(),
-                                     cudaMemcpyHostToDevice, st));
-        AMC_TRY_CUDA(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(Job) * nw, cudaMemcpyHostToDevice, st));
-        AMC_TRY_CUDA(cudaMemsetAsync(arrive_all, 0, sizeof(uint32_t) * arrive_words, st));
-        AMC_TRY_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t), st));
-        KArgs &a = c->args;
-        memset(&a, 0, sizeof(KArgs));
-        a.jobs = jobs_dev;
-        a.n_jobs = nw;
-        a.max_m = max_m;
-        a.max_slots = max_slots;
-        a.jobs_type = opts[wave[0].idx].type;
-        a.total = tiles;
-        a.V = c->V;
-        AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));
-        AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st));
-        std::vector<double> res((size_t)nw * AMC_RES_DOUBLES);
+        ar.top = 0;
+        double *res_dev = nullptr;
+        AMC_TRY(launch_group(c, wopts.data(), wplans.data(), (int)wopts.size(), prec, greeks, ar, st, &res_dev));
+        std::vector<double> res(wopts.size() * AMC_RES_DOUBLES);
         AMC_TRY_CUDA(cudaMemcpyAsync(res.data(), res_dev, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
         AMC_TRY_CUDA(cudaStreamSynchronize(st));
         int wave_status = AMC_OK;
-        for (int k = 0; k < nw; ++k) {
-            int s = result_from(&res[(size_t)k * AMC_RES_DOUBLES], &out[wave[k].idx]);
-            if (s != AMC_OK) wave_status = s;
+        for (size_t k = 0; k < wopts.size(); ++k) {
+            int s2 = result_from(&res[k * AMC_RES_DOUBLES], &out[widx[k]]);
+            if (s2 != AMC_OK) wave_status = s2;
         }
         if (wave_status != AMC_OK) return wave_status;
     }
@@ -402,6 +277,125 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
 }
 
 }  // namespace
+
+namespace amc {
+
+int result_from(const double *r, amc_result *out) {
+    memset(out, 0, sizeof(*out));
+    out->price = r[0];
+    out->std_err = r[1];
+    out->delta = r[2];
+    out->vega = r[3];
+    out->degenerate_dates = (int32_t)r[4];
+    out->status = (int32_t)r[5];
+    return out->status;
+}
+
+GroupKey group_key(const amc_option &o, const SweepPlan &pl) {
+    GroupKey k;
+    k.kind = pl.kind;
+    k.type = pl.kind == 2 ? o.type : 0;
+    k.chunks = pl.chunks;
+    k.lsm = o.rule == AMC_RULE_LSM;
+    return k;
+}
+
+int group_cta_cap(amc_ctx *c, const SweepPlan &pl) {
+    return pl.kind == 2 ? std::min(c->sm_count, kV2MaxCtas) : sweep_ctas_per_sm(pl.chunks) * c->sm_count;
+}
+
+size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec) {
+    const size_t esz = prec == AMC_FP64 ? 8 : 4;
+    size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);            // paths
+    need += pl.kind == 2 ? align_up(v2_xch_units(o.n_steps, pl.ctas) * 8, 256)            // exchange units
+                         : align_up((size_t)o.n_steps * pl.ctas * kNV * 8, 256);          // partials
+    need += 2 * align_up((size_t)o.n_steps * 4, 256);                                      // arrive + shifts
+    need += align_up((size_t)pl.ctas * 32, 256) + align_up(sizeof(Job), 256) + 256;       // fin, job, result
+    return need;
+}
+
+int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int nw, int prec, bool greeks,
+                 SubArena &ar, cudaStream_t st, double **res_out) {
+    const bool fp64 = prec == AMC_FP64;
+    const size_t esz = fp64 ? 8 : 4;
+    const SweepPlan plan0 = plans[0];
+    const bool lsm = opts[0]->rule == AMC_RULE_LSM;
+    std::vector<Job> jobs(nw);
+    Job *jobs_dev;
+    int32_t *status_dev;
+    double *res_dev;
+    uint32_t *arrive_all;
+    AMC_TRY(ar.alloc(sizeof(Job) * nw, (void **)&jobs_dev));
+    AMC_TRY(ar.alloc(sizeof(int32_t), (void **)&status_dev));
+    AMC_TRY(ar.alloc(sizeof(double) * AMC_RES_DOUBLES * nw, (void **)&res_dev));
+    size_t arrive_words = 0;
+    for (int k = 0; k < nw; ++k) arrive_words += opts[k]->n_steps;
+    AMC_TRY(ar.alloc(sizeof(uint32_t) * arrive_words, (void **)&arrive_all));
+    std::vector<uint32_t> shifts;
+    std::vector<size_t> shift_off(nw);
+    for (int k = 0; k < nw; ++k) {
+        shift_off[k] = shifts.size();
+        shifts.resize(shifts.size() + opts[k]->n_steps);
+        host_shifts(opts[k]->seed, opts[k]->n_steps, shifts.data() + shift_off[k]);
+    }
+    uint32_t *shift_dev;
+    AMC_TRY(ar.alloc(sizeof(uint32_t) * shifts.size(), (void **)&shift_dev));
+    int64_t tiles = 0;
+    int cta = 0, max_slots = 1, max_m = 1;
+    size_t arr_off = 0;
+    for (int k = 0; k < nw; ++k) {
+        const amc_option &o = *opts[k];
+        Job &J = jobs[k];
+        fill_job_common(&o, &J);
+        DevBridge *b;
+        AMC_TRY(get_bridge(c, o.n_steps, &b));
+        J.shift = shift_dev + shift_off[k];
+        J.nodes = fp64 ? (const void *)b->nd : (const void *)b->nf;
+        J.nslots = b->nslots;
+        max_slots = std::max(max_slots, b->nslots);
+        max_m = std::max(max_m, o.n_steps);
+        J.ld = host_ld(o.n_paths);
+        AMC_TRY(ar.alloc((size_t)o.n_steps * J.ld * esz, &J.S));
+        J.tile_begin = tiles;
+        J.n_tiles = (o.n_paths + kTilePoints - 1) / kTilePoints;
+        tiles += J.n_tiles;
+        J.cta_begin = cta;
+        J.n_cta = plans[k].ctas;
+        J.chunks = plan0.chunks;
+        cta += J.n_cta;
+        J.greeks = greeks ? 1 : 0;
+        if (plan0.kind == 2) {
+            AMC_TRY(ar.alloc(v2_xch_units(o.n_steps, J.n_cta) * 8, (void **)&J.xch));
+        } else {
+            AMC_TRY(ar.alloc((size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
+        }
+        J.arrive = arrive_all + arr_off;
+        arr_off += o.n_steps;
+        AMC_TRY(ar.alloc((size_t)J.n_cta * 4 * sizeof(double), &J.fin));
+        J.res = res_dev + (size_t)k * AMC_RES_DOUBLES;
+        J.status = status_dev;
+    }
+    AMC_TRY_CUDA(cudaMemcpyAsync(shift_dev, shifts.data(), sizeof(uint32_t) * shifts.size(), cudaMemcpyHostToDevice,
+                                 st));
+    AMC_TRY_CUDA(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(Job) * nw, cudaMemcpyHostToDevice, st));
+    AMC_TRY_CUDA(cudaMemsetAsync(arrive_all, 0, sizeof(uint32_t) * arrive_words, st));
+    AMC_TRY_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t), st));
+    KArgs a;
+    memset(&a, 0, sizeof(KArgs));
+    a.jobs = jobs_dev;
+    a.n_jobs = nw;
+    a.max_m = max_m;
+    a.max_slots = max_slots;
+    a.jobs_type = opts[0]->type;
+    a.total = tiles;
+    a.V = c->V;
+    AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));
+    AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st));
+    *res_out = res_dev;
+    return AMC_OK;
+}
+
+}  // namespace amc
 
 // =================================================================== C ABI
 extern "C" {
@@ -508,6 +502,7 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
 
 int amc_ctx_destroy(amc_ctx *c) {
     if (!c) return AMC_EINVAL;
+    if (c->server) amc_serve_stop(c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &kv : c->bridges) {
@@ -552,6 +547,7 @@ int amc_ctx_memory(amc_ctx *c, size_t *free_bytes, size_t *total_bytes) {
 }
 
 int amc_sobol(amc_ctx *c, int n_dims, int64_t n_points, uint64_t seed, uint32_t *x_dev, int64_t ld, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c || !x_dev || n_dims < 1 || n_dims > AMC_MAX_STEPS || n_points < 0 || n_points > AMC_MAX_PATHS ||
         ld < n_points)
         return AMC_EINVAL;
@@ -564,6 +560,7 @@ int amc_sobol(amc_ctx *c, int n_dims, int64_t n_points, uint64_t seed, uint32_t 
 }
 
 int amc_generate_paths(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, int64_t ld, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     return do_generate(c, opt, prec, S_dev, ld, (cudaStream_t)stream);
@@ -571,6 +568,7 @@ int amc_generate_paths(amc_ctx *c, const amc_option *opt, int prec, void *S_dev,
 
 int amc_sweep(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, int with_greeks,
               double *res_dev, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     return do_sweep(c, opt, prec, S_dev, ld, with_greeks != 0, res_dev, (cudaStream_t)stream);
@@ -578,6 +576,7 @@ int amc_sweep(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, in
 
 int amc_price_device(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, int64_t ld, double *res_dev,
                      void *stream) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     AMC_TRY(do_generate(c, opt, prec, S_dev, ld, (cudaStream_t)stream));
@@ -586,6 +585,7 @@ int amc_price_device(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, i
 
 int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, double T, int n_steps,
                        int64_t n_paths, int basis, int type, uint64_t seed, int rule, int prec, amc_result *out) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c || !out) return AMC_EINVAL;
     amc_option o = make_option(S0, K, r, sigma, T, n_steps, n_paths, basis, type, seed, rule);
     AMC_TRY(host_validate(&o));
@@ -610,12 +610,14 @@ int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, 
 }
 
 int amc_price_batch(amc_ctx *c, const amc_option *opts, int n, int prec, amc_result *out) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c || n < 0 || (n > 0 && (!opts || !out))) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     return run_batch(c, opts, n, prec, false, out);
 }
 
 int amc_greeks(amc_ctx *c, const amc_option *opts, int n, int prec, double *price, double *delta, double *vega) {
+    if (c && c->server) return AMC_EBUSY;
     if (!c || n < 0 || (n > 0 && (!opts || !price || !delta || !vega))) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     std::vector<amc_result> res(n);
