@@ -43,6 +43,9 @@ struct amc_ctx {
     int device = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t bstream[2] = {nullptr, nullptr};   // batch waves, double-buffered
+    double *bres_host[2] = {nullptr, nullptr};       // pinned wave results
+    int batch_cap = 4096;                            // options per wave
     // path arena (bump allocation, reset by each host-level call)
     char *arena = nullptr;
     size_t arena_bytes = 0, arena_top = 0;

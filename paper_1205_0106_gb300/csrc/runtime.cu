@@ -201,9 +201,14 @@ amc_option make_option(double S0, double K, double r, double sigma, double T, in
 }
 
 // ------------------------------------------------------------- batches
-// A wave: options whose paths fit the arena and whose sweep CTAs fit one
-// co-resident launch; within a wave the options share the group key
+// A wave: options whose paths fit half the arena and whose sweep CTAs fit
+// one co-resident launch; within a wave the options share the group key
 // (plan kind, put/call for the mixed LSM kernel, chunk count, rule class).
+// Within a group the options are ordered by date count, so a wave's CTAs
+// finish together.  Waves alternate between two streams and two halves of
+// the arena: the next wave is prepared and launched while the previous one
+// is still on the GPU.  Every option keeps its own CTA group and reduction
+// order, so its result does not depend on the wave it lands in.
 int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, amc_result *out) {
     AMC_TRY(check_prec(prec));
     for (int i = 0; i < n; ++i) {
@@ -223,57 +228,88 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         it.key = group_key(opts[i], it.pl);
         items.push_back(it);
     }
-    // group by key, keeping input order within a group
     std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
         if (a.key.kind != b.key.kind) return a.key.kind < b.key.kind;
         if (a.key.type != b.key.type) return a.key.type < b.key.type;
         if (a.key.chunks != b.key.chunks) return a.key.chunks < b.key.chunks;
-        return a.key.lsm && !b.key.lsm;
+        if (a.key.lsm != b.key.lsm) return a.key.lsm && !b.key.lsm;
+        return opts[a.idx].n_steps > opts[b.idx].n_steps;
     });
     for (int i = 0; i < n; ++i) memset(&out[i], 0, sizeof(amc_result));
+    if (c->inject_kind == 2) {
+        c->inject_kind = 0;
+        return AMC_ENOMEM;
+    }
+    struct Half {
+        cudaStream_t st;
+        SubArena ar;
+        std::vector<int> widx;
+        double *res_host = nullptr;
+        bool busy = false;
+    };
+    Half half[2];
+    const size_t hb = c->arena_bytes / 2 / 4096 * 4096;
+    for (int h = 0; h < 2; ++h) {
+        half[h].st = c->bstream[h];
+        half[h].ar.base = c->arena + h * hb;
+        half[h].ar.size = hb;
+    }
+    int status = AMC_OK;
+    auto finish = [&](Half &H) -> int {
+        if (!H.busy) return AMC_OK;
+        H.busy = false;
+        if (cudaStreamSynchronize(H.st) != cudaSuccess) return AMC_ECUDA;
+        int ws = AMC_OK;
+        for (size_t k = 0; k < H.widx.size(); ++k) {
+            int s2 = result_from(H.res_host + k * AMC_RES_DOUBLES, &out[H.widx[k]]);
+            if (s2 != AMC_OK) ws = s2;
+        }
+        return ws;
+    };
     size_t pos = 0;
-    cudaStream_t st = c->stream;
-    SubArena ar;
-    ar.base = c->arena;
-    ar.size = c->arena_bytes;
-    while (pos < items.size()) {
+    int cur = 0;
+    while (pos < items.size() && status == AMC_OK) {
+        Half &H = half[cur];
+        int rc = finish(H);                                   // this half's previous wave
+        if (rc != AMC_OK) { status = rc; break; }
         const GroupKey key = items[pos].key;
         const int cap = group_cta_cap(c, items[pos].pl);
         std::vector<const amc_option *> wopts;
         std::vector<SweepPlan> wplans;
-        std::vector<int> widx;
+        H.widx.clear();
         size_t bytes = 4096;
         int ctas = 0;
-        while (pos < items.size() && items[pos].key == key) {
+        while (pos < items.size() && items[pos].key == key && (int)wopts.size() < c->batch_cap) {
             const amc_option &o = opts[items[pos].idx];
             const size_t need = option_bytes(o, items[pos].pl, prec);
-            if (!wopts.empty() && (bytes + need > ar.size || ctas + items[pos].pl.ctas > cap)) break;
-            if (bytes + need > ar.size) return AMC_ENOMEM;
+            if (!wopts.empty() && (bytes + need > H.ar.size || ctas + items[pos].pl.ctas > cap)) break;
+            if (bytes + need > H.ar.size) { status = AMC_ENOMEM; break; }
             wopts.push_back(&o);
             wplans.push_back(items[pos].pl);
-            widx.push_back(items[pos].idx);
+            H.widx.push_back(items[pos].idx);
             bytes += need;
             ctas += items[pos].pl.ctas;
             ++pos;
         }
-        if (c->inject_kind == 2) {
-            c->inject_kind = 0;
-            return AMC_ENOMEM;
-        }
-        ar.top = 0;
+        if (status != AMC_OK) break;
+        H.ar.top = 0;
         double *res_dev = nullptr;
-        AMC_TRY(launch_group(c, wopts.data(), wplans.data(), (int)wopts.size(), prec, greeks, ar, st, &res_dev));
-        std::vector<double> res(wopts.size() * AMC_RES_DOUBLES);
-        AMC_TRY_CUDA(cudaMemcpyAsync(res.data(), res_dev, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
-        AMC_TRY_CUDA(cudaStreamSynchronize(st));
-        int wave_status = AMC_OK;
-        for (size_t k = 0; k < wopts.size(); ++k) {
-            int s2 = result_from(&res[k * AMC_RES_DOUBLES], &out[widx[k]]);
-            if (s2 != AMC_OK) wave_status = s2;
+        rc = launch_group(c, wopts.data(), wplans.data(), (int)wopts.size(), prec, greeks, H.ar, H.st, &res_dev);
+        if (rc != AMC_OK) { status = rc; break; }
+        H.res_host = c->bres_host[cur];
+        if (cudaMemcpyAsync(H.res_host, res_dev, sizeof(double) * AMC_RES_DOUBLES * wopts.size(),
+                            cudaMemcpyDeviceToHost, H.st) != cudaSuccess) {
+            status = AMC_ECUDA;
+            break;
         }
-        if (wave_status != AMC_OK) return wave_status;
+        H.busy = true;
+        cur ^= 1;
     }
-    return AMC_OK;
+    for (int h = 0; h < 2; ++h) {
+        int rc = finish(half[h]);
+        if (status == AMC_OK) status = rc;
+    }
+    return status;
 }
 
 }  // namespace
@@ -458,7 +494,14 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
             rc = AMC_ECUDA;
             break;
         }
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = AMC_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->bstream[0], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->bstream[1], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&c->bres_host[0], sizeof(double) * AMC_RES_DOUBLES * c->batch_cap) != cudaSuccess ||
+            cudaMallocHost(&c->bres_host[1], sizeof(double) * AMC_RES_DOUBLES * c->batch_cap) != cudaSuccess) {
+            rc = AMC_ECUDA;
+            break;
+        }
         std::vector<uint32_t> V((size_t)AMC_MAX_STEPS * 32);
         if (host_directions(AMC_MAX_STEPS, V.data()) != AMC_OK) { rc = AMC_EINVAL; break; }
         if (cudaMalloc(&c->V, V.size() * 4) != cudaSuccess ||
@@ -522,6 +565,10 @@ int amc_ctx_destroy(amc_ctx *c) {
     for (int k = 0; k < 3; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->stream) cudaStreamDestroy(c->stream);
+    for (int h = 0; h < 2; ++h) {
+        if (c->bstream[h]) cudaStreamDestroy(c->bstream[h]);
+        if (c->bres_host[h]) cudaFreeHost(c->bres_host[h]);
+    }
     delete c;
     return AMC_OK;
 }
