@@ -129,7 +129,7 @@ int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *righ
  * under `rule` (a pure function of these and the device's SM count), and
  * the paths each sweep thread owns.  AMC_EINVAL when the option's per-path
  * state does not fit on chip: the mixed LSM sweep holds up to
- * min(SMs, 160) * 7936 paths (1.2 M on 152 SMs), the other sweeps up to
+ * min(SMs, 160) * 7680 paths (1.17 M on 152 SMs), the other sweeps up to
  * SMs * 8192.                                                              */
 int amc_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, int32_t *ctas, int32_t *paths_per_thread);
 

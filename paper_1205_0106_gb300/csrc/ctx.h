@@ -67,6 +67,7 @@ struct amc_ctx {
     double *res_host = nullptr;                      // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     double timeout_s = 2.0;
+    uint32_t poll_ns = 0;                            // exchange poll back-off, ns (AMC_POLL_NS overrides)
     int inject_kind = 0;
     int64_t inject_arg = 0;
     std::mutex mu;                                   // launches and tables

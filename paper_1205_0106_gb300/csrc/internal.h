@@ -88,12 +88,12 @@ struct Job {
 
 constexpr int kNV = 12;             // cross-CTA values per date: 2p-1 moments + p RHS (p <= 4)
 
-// Mixed-precision LSM sweep (sweep_v2.cu): 1 solver warp + 31 path warps,
+// Mixed-precision LSM sweep (sweep_v2.cu): 2 solver warps + 30 path warps,
 // 8 paths per path thread, a ring of 5 date slices in shared memory.
 constexpr int kV2Threads = 1024;
-constexpr int kV2Workers = 992;
+constexpr int kV2Workers = 960;
 constexpr int kV2PPT = 8;
-constexpr int kV2PathsPerCta = kV2Workers * kV2PPT;   // 7936
+constexpr int kV2PathsPerCta = kV2Workers * kV2PPT;   // 7680
 constexpr int kV2Slots = 5;
 constexpr int kXV = 11;             // exchanged values per date: 7 moment slots + 4 RHS slots
 constexpr uint32_t kEpochBits = 22; // tag = epoch << 10 | exchange index
@@ -116,6 +116,7 @@ struct KArgs {
     const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
     uint64_t timeout_ns;
     uint32_t epoch;                 // launch tag of the mixed LSM sweep's exchange units
+    uint32_t poll_ns;               // back-off between exchange polls (mixed LSM sweep)
     Job one;
     uint32_t shift_one[AMC_MAX_STEPS];
 };

@@ -113,6 +113,7 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
             g_epoch[dev] = 1;
         }
         a.epoch = g_epoch[dev];
+        a.poll_ns = 0;
     }
     const bool fp64 = prec == AMC_FP64;
     cudaError_t e = pl.kind == 2 ? launch_sweep_lsm_v2(a, pl.ctas, with_greeks != 0, st)

@@ -4,6 +4,7 @@
 // the kernels of pathgen.cu and sweep.cu; this file only plans and launches.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -101,6 +102,7 @@ int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, boo
     cudaError_t e;
     if (pl.kind == 2) {
         a.epoch = next_epoch(c);
+        a.poll_ns = c->poll_ns;
         e = launch_sweep_lsm_v2(a, total_ctas, greeks, st);
     } else if (lsm) {
         e = launch_sweep_lsm(a, total_ctas, pl.chunks, fp64, greeks, st);
@@ -490,6 +492,7 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
     c->device = device;
     int rc = AMC_OK;
     do {
+        if (const char *e = getenv("AMC_POLL_NS")) c->poll_ns = (uint32_t)strtoul(e, nullptr, 10);
         if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
             rc = AMC_ECUDA;
             break;

@@ -46,23 +46,28 @@ constexpr int kSlots = kV2Slots;
 constexpr int kMaxCtas = 160;               // exchange gather: 5 units per lane
 constexpr unsigned kFull = 0xffffffffu;
 
+constexpr int kSolvers = 2;                 // solver warps 0 and 1 take alternate dates
+constexpr int kW0 = 32 * kSolvers;          // first path thread
+constexpr int kXW0 = kSolvers;              // exchange warps kXW0 .. kXW0+10
+
 struct SmemV2 {
     float S[kSlots][kPPC];
     uint64_t mbar[kSlots];
-    float redG[2][32][7];           // warp sums of Gram moments, by exchange parity
-    float redR[32][4];              // warp sums of right-hand sides
+    float redG[2][32][7];           // warp sums of Gram moments (Gram warps), by exchange parity
+    float redR[32][4];              // warp sums of right-hand sides (path warps)
     float red[32][4];               // final sums
-    double tot[kXV];
-    double gtot[3][8];
-    double ginv[3][16];
-    double beta[4];
-    double sA[16];
-    double sP[4];
+    float tot_hi[kXV], tot_lo[kXV]; // exchange totals (double-float)
+    double gtot[3][8];              // Gram totals by date mod 3
+    double ginv[3][16];             // inverse Gram matrix (FP64) by date mod 3
+    float ginv_hi[3][16], ginv_lo[3][16];  // the same as double-float for the path warps
+    float beta[4];
+    double sA[kSolvers][16];
+    double sP[kSolvers][4];
     int gdeg[3];
     int deg_cur;                    // degenerate flag of the coefficients in beta
     int pend[kSlots];
-    volatile int gready;
-    volatile int ginv_ready;
+    volatile int gtot_date[3];      // date whose Gram totals are in gtot[b]
+    volatile int ginv_date[3];      // date whose inverse is in ginv*[b]
     volatile int abort;
 };
 
@@ -143,6 +148,7 @@ __device__ __forceinline__ double det3(double a00, double a01, double a02, doubl
 
 __device__ __forceinline__ double gram_inverse(const double *M, int p, int lane, double *sA, double *sP,
                                                bool &deg) {
+    // (sA, sP: this solver warp's staging area)
     // power-of-two scale factors P_k ~ 1/sqrt(M_2k) (exact), scaled matrix in shared memory
     if (lane < 4) {
         int e = 0;
@@ -221,6 +227,16 @@ __device__ __forceinline__ float warp_sum4(const float (&v)[4], int lane) {
     return r;
 }
 
+// Double-float product of a (Ginv entry) and b (total), a.hi*b.hi exact via FMA.
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = __fadd_rn(p, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
 template <bool GREEKS, bool PUT>
 __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_constant__ KArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -236,33 +252,42 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     const int64_t base = (int64_t)lc * kPPC;
     const int64_t rem = ld - base;
     const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * 4u;
+    const int nloc = (N - base) < kPPC ? (int)(N - base) : kPPC;      // own paths below N
     uint64_t *const xch = J.xch;
     int32_t *const status = J.status;
     const uint64_t timeout_ns = a.timeout_ns;
     const uint32_t tag_hi = a.epoch << 10;
     const int inject_date = (lc == 0 && jb == 0) ? J.inject_date : 0;
+    const unsigned poll_ns = a.poll_ns;
 
     if (tid == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(&sm.mbar[s], 1);
             sm.pend[s] = 0;
         }
-        sm.gready = m + 1;
-        sm.ginv_ready = m + 1;
+        for (int b = 0; b < 3; ++b) {
+            sm.gtot_date[b] = 0;
+            sm.ginv_date[b] = 0;
+        }
         sm.deg_cur = 0;
-        for (int k = 0; k < 4; ++k) sm.beta[k] = 0.0;
+        for (int k = 0; k < 4; ++k) sm.beta[k] = 0.f;
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
     __syncthreads();
 
-    // ------------------------------------------------------------ solver warp
-    if (warp == 0) {
-        for (int d = m - 1; d >= 1; --d) {
+    // ----------------------------------------------------------- solver warps
+    // Warp q handles the dates d = m-1-q, m-1-q-2, ...: it waits for the
+    // date's Gram totals (double-float, from an exchange two dates earlier),
+    // forms them in FP64 and inverts; the path warps pick the result up when
+    // they reach that date.
+    if (warp < kSolvers) {
+        for (int d = m - 1 - warp; d >= 1; d -= kSolvers) {
+            const int b = d % 3;
             const uint64_t t0 = globaltimer();
             bool bail = false;
-            while (sm.gready > d) {
+            while (sm.gtot_date[b] != d) {
                 if (sm.abort || ld_volatile_int(status) != 0 || globaltimer() - t0 > timeout_ns) {
                     bail = true;
                     break;
@@ -278,14 +303,18 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 return;
             }
             __threadfence_block();
-            const int b = d % 3;
             bool deg;
-            const double gi = gram_inverse(sm.gtot[b], p, lane, sm.sA, sm.sP, deg);
-            if (lane < 16) sm.ginv[b][lane] = gi;
+            const double gi = gram_inverse(sm.gtot[b], p, lane, sm.sA[warp], sm.sP[warp], deg);
+            if (lane < 16) {
+                sm.ginv[b][lane] = gi;
+                const float hi = (float)gi;
+                sm.ginv_hi[b][lane] = hi;
+                sm.ginv_lo[b][lane] = (float)(gi - (double)hi);
+            }
             if (lane == 0) sm.gdeg[b] = deg ? 1 : 0;
             __syncwarp();
             __threadfence_block();
-            if (lane == 0) sm.ginv_ready = d;
+            if (lane == 0) sm.ginv_date[b] = d;
         }
         return;
     }
@@ -296,7 +325,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // copied from HBM until the Gram pass of that date rewrites them in place
     // as y for in-the-money own paths and 0 otherwise; later passes then need
     // no payoff, moneyness or validity arithmetic (ITM <=> y != 0).
-    const int w = tid - 32;
+    // Per date all 30 path warps run the exercise and right-hand-side pass
+    // and, after the post, the Gram pass of a later date over their own 8
+    // paths; warps kXW0..kXW0+10 also post and gather one exchanged value
+    // each.
+    const int w = tid - kW0;
     auto issue = [&](int d) {            // w == 0 only
         const int s = d % kSlots;
         fence_proxy_async();
@@ -318,12 +351,8 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if (w == 0) sm.pend[s] = 0;
         return true;
     };
-    uint32_t valid = 0;                  // own paths below N (ragged last CTA)
-#pragma unroll
-    for (int i = 0; i < kPPT; ++i)
-        if (base + w + i * kWorkers < N) valid |= 1u << i;
-    // Gram pass of date d: y in place, in-the-money moments summed over the
-    // warp into sm.redG[buf][warp][k]
+    // Gram pass of date d over the own paths: y in place, in-the-money
+    // moments summed over the warp into sm.redG[buf][warp][k]
     auto gram_post = [&](int d, int buf) {
         float g[8];
 #pragma unroll
@@ -331,11 +360,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         float *sl = sm.S[d % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
-            const float s = sl[w + i * kWorkers];
-            const float yr = fmaf(s, invK, -1.f);
-            const bool itm = ((valid >> i) & 1u) && (PUT ? yr < 0.f : yr > 0.f);
+            const int idx = w + i * kWorkers;
+            const float yr = fmaf(sl[idx], invK, -1.f);
+            const bool itm = idx < nloc && (PUT ? yr < 0.f : yr > 0.f);
             const float y = itm ? yr : 0.f;
-            sl[w + i * kWorkers] = y;
+            sl[idx] = y;
             const float y2 = y * y, y3 = y2 * y;
             g[0] += itm ? 1.f : 0.f;
             g[1] += y;
@@ -363,9 +392,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         const float *sl = sm.S[m % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
-            const float y = fmaf(sl[w + i * kWorkers], invK, -1.f);
+            const int idx = w + i * kWorkers;
+            const float y = fmaf(sl[idx], invK, -1.f);
             const float h = PUT ? -y : y;
-            cf[i] = (((valid >> i) & 1u) && h > 0.f) ? h : 0.f;
+            cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
             if (GREEKS) { tau[i] = m; yt[i] = y; }
         }
     }
@@ -401,7 +431,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 if (sm.deg_cur) {
                     if (w == 0) ++degenerate;
                 } else {
-                    exercise(j + 1, (float)sm.beta[0], (float)sm.beta[1], (float)sm.beta[2], (float)sm.beta[3]);
+                    exercise(j + 1, sm.beta[0], sm.beta[1], sm.beta[2], sm.beta[3]);
                 }
             }
             float rr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -424,14 +454,17 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         const uint32_t mask = (hasG ? ((1u << nmom) - 1u) : 0u) | (hasR ? (((1u << p) - 1u) << 7) : 0u);
         bar_work();                                               // B1
         if (w == 0 && j + 1 <= m - 1 && j + 1 - kSlots >= 1) issue(j + 1 - kSlots);   // slice j+1 consumed
-        // cross-CTA exchange: warp 1+k owns value slot k; it posts first, then
-        // does its share of the next Gram pass, then gathers
+        // cross-CTA exchange: warp kXW0+k owns value slot k; it posts, runs
+        // its share of the next Gram pass (which also absorbs the other
+        // CTAs' lag), then gathers
         const uint32_t tag = tag_hi | (uint32_t)j;
-        const bool xw = warp >= 1 && warp <= kXV && ((mask >> (warp - 1)) & 1u);
-        const int xk = warp - 1;
+        const int xk = warp - kXW0;
+        const bool xw = xk >= 0 && xk < kXV && ((mask >> xk) & 1u);
         uint64_t *xu = xch + ((size_t)j * kXV + (xw ? xk : 0)) * G;
         if (xw) {
-            const float pv = lane < 31 ? (xk < 7 ? sm.redG[j & 1][lane + 1][xk] : sm.redR[lane + 1][xk - 7]) : 0.f;
+            float pv = 0.f;
+            if (xk < 7) pv = lane < 32 - kXW0 ? sm.redG[j & 1][kXW0 + lane][xk] : 0.f;
+            else pv = lane < 32 - kXW0 ? sm.redR[kXW0 + lane][xk - 7] : 0.f;
             dfl part = df_warp_sum(dfl{pv, 0.f});
             if (lane == 0 && inject_date != j)
                 st_unit(xu + lc, ((uint64_t)tag << 32) | __float_as_uint(__fadd_rn(part.hi, part.lo)));
@@ -461,27 +494,33 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                     }
                     break;
                 }
+                __nanosleep(poll_ns);    // back off: all CTAs poll the same lines
             }
             dfl acc = {0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < kMaxCtas / 32; ++q)
                 if (lane + 32 * q < G) acc = df_add(acc, dfl{vals[q], 0.f});
             acc = df_warp_sum(acc);
-            if (lane == 0) sm.tot[xk] = (double)acc.hi + (double)acc.lo;
+            if (lane == 0) {
+                sm.tot_hi[xk] = acc.hi;
+                sm.tot_lo[xk] = acc.lo;
+            }
         }
         stop = bar_work_any(sm.abort);                            // B2
         if (stop) break;
-        if (hasG && w == 0) {                                     // Gram totals of date j-2 -> solver
+        if (hasG && warp == kXW0 + 1 && lane < 7) {               // Gram totals of date j-2 -> solver
             const int b = (j - 2) % 3;
-            for (int k = 0; k < 7; ++k) sm.gtot[b][k] = sm.tot[k];
+            sm.gtot[b][lane] = (double)sm.tot_hi[lane] + (double)sm.tot_lo[lane];
+            __syncwarp(0x7fu);
             __threadfence_block();
-            sm.gready = j - 2;
+            if (lane == 0) sm.gtot_date[b] = j - 2;
         }
         if (hasR) {
-            if (warp == 1) {
+            if (warp == kXW0) {
+                const int b = j % 3;
                 const uint64_t t0 = globaltimer();
                 bool bail = false;
-                while (sm.ginv_ready > j) {
+                while (sm.ginv_date[b] != j) {
                     if (sm.abort || globaltimer() - t0 > timeout_ns) {
                         bail = true;
                         break;
@@ -492,13 +531,16 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                     sm.abort = 1;
                 }
                 __threadfence_block();
-                const int b = j % 3;
-                // beta_k = sum_l Ginv_kl R_l: lane 4k+l one product, then two butterfly steps
+                // beta_k = sum_l Ginv_kl R_l in double-float: lane 4k+l one product,
+                // then two butterfly steps
                 const int bl = lane & 3;
-                double t = (lane < 16 && bl < p) ? sm.ginv[b][lane] * sm.tot[7 + bl] : 0.0;
-                t += __shfl_xor_sync(kFull, t, 1);
-                t += __shfl_xor_sync(kFull, t, 2);
-                if (lane < 16 && bl == 0) sm.beta[lane >> 2] = t;
+                dfl t = {0.f, 0.f};
+                if (lane < 16 && bl < p)
+                    t = df_mul(dfl{sm.ginv_hi[b][lane], sm.ginv_lo[b][lane]},
+                               dfl{sm.tot_hi[7 + bl], sm.tot_lo[7 + bl]});
+                t = df_add(t, df_shfl_xor(t, 1));
+                t = df_add(t, df_shfl_xor(t, 2));
+                if (lane < 16 && bl == 0) sm.beta[lane >> 2] = __fadd_rn(t.hi, t.lo);
                 if (lane == 0) sm.deg_cur = sm.gdeg[b];
             }
             stop = bar_work_any(sm.abort);                        // B3
@@ -510,7 +552,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if (sm.deg_cur) {
             if (w == 0) ++degenerate;
         } else {
-            exercise(1, (float)sm.beta[0], (float)sm.beta[1], (float)sm.beta[2], (float)sm.beta[3]);
+            exercise(1, sm.beta[0], sm.beta[1], sm.beta[2], sm.beta[3]);
         }
     }
 
@@ -537,7 +579,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     const float mu = r - 0.5f * sig * sig;
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
-        if (!((valid >> i) & 1u)) continue;
+        if (w + i * kWorkers >= nloc) continue;
         fs[0] += cf[i];
         fs[1] += cf[i] * cf[i];
         if (GREEKS && cf[i] > 0.f) {
@@ -556,9 +598,9 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if ((lane & 7) == 0) sm.red[warp][k] = rsum;
     }
     bar_work();
-    if (warp >= 1 && warp <= 4) {
-        const int k = warp - 1;
-        dfl part = {lane < 31 ? sm.red[lane + 1][k] : 0.f, 0.f};
+    if (warp >= kXW0 && warp < kXW0 + 4) {
+        const int k = warp - kXW0;
+        dfl part = {lane < 32 - kXW0 ? sm.red[kXW0 + lane][k] : 0.f, 0.f};
         part = df_warp_sum(part);
         const double scale = k == 0 ? J.K : (k == 1 ? J.K * J.K : 1.0);
         if (lane == 0)

@@ -99,9 +99,9 @@ def test_sweep_plan_is_a_function_of_paths(amc):
         assert ctas * 256 * ppt < n + 256 * ppt + 1
         assert ppt in (4, 8, 16, 32)
         ctas, ppt = amc.amc_plan_sweep(n, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM)
-        assert ppt == 8 and ctas == -(-n // 7936) and ctas <= 152
+        assert ppt == 8 and ctas == -(-n // 7680) and ctas <= 152
     assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_FP64, amc.AMC_RULE_LSM) == (512, 8)
-    assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM) == (133, 8)
+    assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM) == (137, 8)
     assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_MIXED, amc.AMC_RULE_EUROPEAN) == (512, 8)
     for prec in (amc.AMC_FP64, amc.AMC_MIXED):
         with pytest.raises(amc.AmcError):
