@@ -46,6 +46,22 @@ def _config(opt, extra=None):
     return c
 
 
+def replica_option(opt, rank):
+    """The option rank `rank` prices in a multi-GPU run: the same contract with
+    its own digital shift (seed + rank), so replicas do independent work."""
+    return workloads.Option(**{**opt.as_dict(), "seed": opt.seed + rank})
+
+
+def max_over_ranks(dist, value, device="cpu"):
+    """Largest `value` over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -101,6 +117,26 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def profile_traffic(kernel_src, summary):
+    """DRAM bytes per launch recorded in a committed ncu summary, or None when
+    the kernel source has changed since that capture (hash mismatch)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, kernel_src), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        vals = {}
+        with open(os.path.join(ROOT, summary)) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
+        if vals.get("source_sha256_16") != h:
+            return None
+        return int(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -210,7 +246,7 @@ def run_amc(args):
 
     opt = workloads.single_large()
     if ws > 1:
-        opt = workloads.Option(**{**opt.as_dict(), "seed": opt.seed + rank})
+        opt = replica_option(opt, rank)
     ctx = amc.Context(local, arena_bytes=4 << 30)
     stream = torch.cuda.Stream()
     ld = amc.amc_path_ld(opt.n_paths)
@@ -263,10 +299,7 @@ def run_amc(args):
     clocks.start()
     t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
     ck = clocks.stop()
-    t_tensor = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    t_ms = float(t_tensor.item())
+    t_ms = max_over_ranks(dist, t_ms, "cuda")
     ms_per_step = t_ms / args.steps
     value = units * ws / (ms_per_step * 1e-3)
     price = amc.res_to_dict(res.cpu().numpy())
@@ -289,10 +322,7 @@ def run_amc(args):
         amc.amc_price_american(ctx, opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, opt.basis,
                                opt.type, opt.seed, opt.rule, amc.AMC_MIXED)
     e2e_s = time.perf_counter() - t0
-    e_tensor = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e_tensor, op=dist.ReduceOp.MAX)
-    e2e_value = units * ws * args.steps / float(e_tensor.item())
+    e2e_value = units * ws * args.steps / max_over_ranks(dist, e2e_s, "cuda")
 
     if rank != 0:
         if dist is not None:
@@ -305,9 +335,14 @@ def run_amc(args):
     sweep_gbs = bytes_sweep / (sweep_ms * 1e-3) / 1e9
     gen_gbs = bytes_gen / (gen_ms * 1e-3) / 1e9
     rl_sweep = {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s", "frac": sweep_gbs / hbm,
-                "traffic": None, "kernel": "sweep_lsm_kernel", "ms": sweep_ms, "peak_kind": peak_kind}
+                "traffic": profile_traffic("paper_1205_0106_gb300/csrc/sweep_v2.cu",
+                                           "profiles/sweep_lsm_v2_2p20x252_mixed.md"),
+                "kernel": "sweep_lsm_v2_kernel", "ms": sweep_ms, "peak_kind": peak_kind,
+                "algorithmic_bytes": bytes_sweep}
     rl_gen = {"bound": "hbm", "achieved": gen_gbs, "peak": hbm, "unit": "GB/s", "frac": gen_gbs / hbm,
-              "traffic": None, "kernel": "pathgen_kernel", "ms": gen_ms, "peak_kind": peak_kind}
+              "traffic": profile_traffic("paper_1205_0106_gb300/csrc/pathgen.cu", "profiles/pathgen_2p20x252_mixed.md"),
+              "kernel": "pathgen_kernel", "ms": gen_ms, "peak_kind": peak_kind, "algorithmic_bytes": bytes_gen,
+              "note": "issue-bound (ALU); the HBM write fraction is the secondary bound"}
     dominant = rl_gen if gen_ms >= sweep_ms else rl_sweep
     err = None
     if not args.no_oracle_check:
