@@ -12,7 +12,9 @@ L2, so every step streams it from HBM.
 Keys beyond the base contract: fp64 (the same step in all-FP64 on the GPU),
 err_vs_oracle (|price - FP64 oracle price| on identical points, in units of
 K), roofline (dominant kernel) and roofline_sweep, cpu_baseline (the oracle
-on a bounded sample, host cores), clocks.
+on a bounded sample, host cores), clocks, serving (a Poisson request replay),
+batch and greeks (the 4096-option batch and 1024-option Greeks workloads
+through their host calls).
 
 Multi-GPU (torchrun, N>1): independent replicas, one option per rank (shift
 seed 2 + rank), no collective on the data path; value sums all ranks.
@@ -148,9 +150,13 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(opt, n_sample=2 ** 16):
-    """The FP64 oracle as it stands on a bounded sample (first n_sample paths)."""
+def cpu_baseline(opt, n_sample=None):
+    """The FP64 oracle as it stands on a bounded sample (first n_sample paths; default all of them,
+    about 5 s on 16 host cores). A 64-path call first loads the library and its tables."""
     import oracle
+    n_sample = opt.n_paths if n_sample is None else n_sample
+    oracle.lsm(oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, 64, opt.seed),
+               opt.type, opt.K, opt.r, opt.T, opt.basis)
     t = time.perf_counter()
     S = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, n_sample, opt.seed)
     oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
@@ -158,6 +164,47 @@ def cpu_baseline(opt, n_sample=2 ** 16):
     return {"value": n_sample * opt.n_steps / dt, "unit": METRIC, "cores": oracle.threads(), "kind": "oracle",
             "sample": "first %d of %d paths, all %d dates, paths + LSM sweep, %.1f s" % (
                 n_sample, opt.n_paths, opt.n_steps, dt)}
+
+
+def batch_and_greeks(amc, device, reps=2, n_check=8):
+    """The 4096-option batch and the 1024-option Greeks workloads through their host calls
+    (host buffers in and out, so wall time), each after one warm-up call; the batch price
+    of a seeded sample of n_check options is checked against the FP64 oracle."""
+    import numpy as np
+    bctx = amc.Context(device, arena_bytes=32 << 30)
+    out = {}
+    opts = workloads.batch_options()
+    steps = sum(o.path_steps for o in opts)
+    amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+    t = time.perf_counter()
+    for _ in range(reps):
+        res = amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+    dt = (time.perf_counter() - t) / reps
+    failed = sum(r["status"] != 0 for r in res)
+    out["batch"] = {"options": len(opts), "path_steps": steps, "s": dt, "value": steps / dt, "unit": METRIC,
+                    "failed": failed, "workload": "4096 options, seed 3, 2^14..2^18 paths, 12..365 dates, p = 3"}
+    if n_check:
+        import oracle
+        idx = np.random.default_rng(7).choice(len(opts), n_check, replace=False)
+        errs = []
+        for i in idx:
+            o = opts[i]
+            ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
+                               seed=o.seed)
+            errs.append(abs(res[i]["price"] - ref["price"]) / o.K)
+        out["batch"]["oracle_sample"] = n_check
+        out["batch"]["oracle_max_err_over_K"] = max(errs)
+    gopts = workloads.greeks_options()
+    gsteps = sum(o.path_steps for o in gopts)
+    amc.amc_greeks(bctx, gopts, amc.AMC_MIXED)
+    t = time.perf_counter()
+    for _ in range(reps):
+        amc.amc_greeks(bctx, gopts, amc.AMC_MIXED)
+    dt = (time.perf_counter() - t) / reps
+    out["greeks"] = {"options": len(gopts), "path_steps": gsteps, "s": dt, "value": gsteps / dt, "unit": METRIC,
+                     "workload": "1024 puts, seed 5, 2^18 paths, 100 dates, price + delta + vega"}
+    bctx.close()
+    return out
 
 
 def serve_replay(amc, ctx, times, opts, slots=3, max_batch=128, prec=1):
@@ -371,6 +418,8 @@ def run_amc(args):
         sv["workload"] = "Poisson 2000 req/s, %.0f s of the seed-4 request stream" % args.serve_seconds
         line["serving"] = sv
         sctx.close()
+    if not args.no_batch:
+        line.update(batch_and_greeks(amc, local))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(opt)
     print(json.dumps(line), flush=True)
@@ -388,6 +437,7 @@ def main():
     ap.add_argument("--impl", choices=["amc", "reference"], default="amc")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch and Greeks workloads")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
