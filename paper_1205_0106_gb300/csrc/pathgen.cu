@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "devutil.cuh"
 #include "internal.h"
 
 namespace amc {
@@ -71,6 +72,24 @@ __device__ __forceinline__ float icdf_central(float y) {
     a = fmaf(a, wc, 6.976040602e-01f);
     a = fmaf(a, wc, 4.246626854e+00f);
     return y * a;
+}
+// The same for two points in packed f32x2 arithmetic (identical rounding).
+__device__ __forceinline__ dev::f2 icdf_central2(dev::f2 y) {
+    using namespace dev;
+    const f2 t = f2_fma(f2_mul(y, f2_splat(-4.f)), y, f2_splat(1.f));
+    const f2 l = f2_pack(lg2_approx(f2_lo(t)), lg2_approx(f2_hi(t)));
+    const f2 wc = f2_fma(f2_splat(-0.693147181f), l, f2_splat(-2.5f));
+    f2 a = f2_splat(-2.471926130e-08f);
+    a = f2_fma(a, wc, f2_splat(6.586265044e-08f));
+    a = f2_fma(a, wc, f2_splat(1.316422299e-06f));
+    a = f2_fma(a, wc, f2_splat(-9.795854567e-06f));
+    a = f2_fma(a, wc, f2_splat(-1.402823636e-05f));
+    a = f2_fma(a, wc, f2_splat(6.175783346e-04f));
+    a = f2_fma(a, wc, f2_splat(-3.543307772e-03f));
+    a = f2_fma(a, wc, f2_splat(-1.181544270e-02f));
+    a = f2_fma(a, wc, f2_splat(6.976040602e-01f));
+    a = f2_fma(a, wc, f2_splat(4.246626854e+00f));
+    return f2_mul(y, a);
 }
 // Tails: p = min(u, 1-u) from x or its complement.
 __device__ __noinline__ float icdf_tail(uint32_t x, float y) {
@@ -211,32 +230,53 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
             const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
             R4<Real> Wo, So;
-            Real z[4];
             if (FP64) {
+                Real z[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) z[q] = (Real)normcdfinv(((double)xq[q] + 0.5) * 0x1p-32);
-            } else {
-                // the four central-region values straight-line, then the rare tails
-                float yv[4];
-                bool tail = false;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    yv[q] = icdf_y(xq[q]);
-                    z[q] = (Real)icdf_central(yv[q]);
-                    tail |= !(fabsf(yv[q]) < 0.4983f);
+                    const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
+                    Wo.v[q] = W;
+                    So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
                 }
+            } else {
+                // points (0, 1) and (2, 3) as packed pairs: central-region
+                // values straight-line, then the rare tails, then bridge and GBM
+                using namespace dev;
+                float z[4], yv[4];
+                bool tail = false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const f2 y = f2_fma(f2_pack((float)(int32_t)(xq[2 * h] ^ 0x80000000u),
+                                                (float)(int32_t)(xq[2 * h + 1] ^ 0x80000000u)),
+                                        f2_splat(0x1p-32f), f2_splat(0x1p-33f));
+                    const f2 zc = icdf_central2(y);
+                    yv[2 * h] = f2_lo(y);
+                    yv[2 * h + 1] = f2_hi(y);
+                    z[2 * h] = f2_lo(zc);
+                    z[2 * h + 1] = f2_hi(zc);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < 0.4983f);
                 if (tail) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (!(fabsf(yv[q]) < 0.4983f)) z[q] = (Real)icdf_tail(xq[q], yv[q]);
+                        if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q], yv[q]);
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
-                Wo.v[q] = W;
-                if (FP64) So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
-                else So.v[q] = S0 * ex2_approx((float)fma(sig, W, drift));
+                for (int h = 0; h < 2; ++h) {
+                    const f2 W = f2_fma(f2_splat((float)sd), f2_pack(z[2 * h], z[2 * h + 1]),
+                                        f2_fma(f2_splat((float)wr), f2_pack((float)Wr.v[2 * h], (float)Wr.v[2 * h + 1]),
+                                               f2_mul(f2_splat((float)wl),
+                                                      f2_pack((float)Wl.v[2 * h], (float)Wl.v[2 * h + 1]))));
+                    const f2 e = f2_fma(f2_splat((float)sig), W, f2_splat((float)drift));
+                    const f2 Sv = f2_mul(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))));
+                    Wo.v[2 * h] = (Real)f2_lo(W);
+                    Wo.v[2 * h + 1] = (Real)f2_hi(W);
+                    So.v[2 * h] = (Real)f2_lo(Sv);
+                    So.v[2 * h + 1] = (Real)f2_hi(Sv);
+                }
             }
             s_W[nd.so * kPathgenThreads + tid] = Wo;
             if (store) {

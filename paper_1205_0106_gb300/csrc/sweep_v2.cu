@@ -330,6 +330,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // paths; warps kXW0..kXW0+10 also post and gather one exchanged value
     // each.
     const int w = tid - kW0;
+    // path thread w owns the pairs 2w, 2w+1 (+ 2 * 960 i, i = 0..3) of the
+    // CTA's slice: one 8-byte shared-memory access and packed f32x2
+    // arithmetic per pair
+    auto pidx = [&](int i) { return 2 * w + (i & 1) + (i >> 1) * (2 * kWorkers); };
     auto issue = [&](int d) {            // w == 0 only
         const int s = d % kSlots;
         fence_proxy_async();
@@ -359,20 +363,26 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         for (int k = 0; k < 8; ++k) g[k] = 0.f;
         float *sl = sm.S[d % kSlots];
 #pragma unroll
-        for (int i = 0; i < kPPT; ++i) {
-            const int idx = w + i * kWorkers;
-            const float yr = fmaf(sl[idx], invK, -1.f);
-            const bool itm = idx < nloc && (PUT ? yr < 0.f : yr > 0.f);
-            const float y = itm ? yr : 0.f;
-            sl[idx] = y;
-            const float y2 = y * y, y3 = y2 * y;
-            g[0] += itm ? 1.f : 0.f;
-            g[1] += y;
-            g[2] += y2;
-            g[3] += y3;
-            g[4] = fmaf(y2, y2, g[4]);
-            g[5] = fmaf(y2, y3, g[5]);
-            g[6] = fmaf(y3, y3, g[6]);
+        for (int i = 0; i < kPPT; i += 2) {
+            const int idx = pidx(i);
+            const float2 s2 = *reinterpret_cast<const float2 *>(sl + idx);
+            float2 y2;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const float yr = fmaf(h2 ? s2.y : s2.x, invK, -1.f);
+                const bool itm = idx + h2 < nloc && (PUT ? yr < 0.f : yr > 0.f);
+                const float y = itm ? yr : 0.f;
+                (h2 ? y2.y : y2.x) = y;
+                const float yy = y * y, y3 = yy * y;
+                g[0] += itm ? 1.f : 0.f;
+                g[1] += y;
+                g[2] += yy;
+                g[3] += y3;
+                g[4] = fmaf(yy, yy, g[4]);
+                g[5] = fmaf(yy, y3, g[5]);
+                g[6] = fmaf(y3, y3, g[6]);
+            }
+            *reinterpret_cast<float2 *>(sl + idx) = y2;
         }
         fence_proxy_async();             // these generic writes precede a later TMA refill
         const float r = warp_sum8(g, lane);
@@ -392,7 +402,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         const float *sl = sm.S[m % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
-            const int idx = w + i * kWorkers;
+            const int idx = pidx(i);
             const float y = fmaf(sl[idx], invK, -1.f);
             const float h = PUT ? -y : y;
             cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
@@ -405,18 +415,35 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     if (m >= 2 && !stop && wait_slice(m - 1)) gram_post(m - 1, (m + 1) & 1);
 
     // exercise at date d with the coefficients in sm.beta
+    // (packed f32x2 pairs; the Greeks variant, which also carries the
+    // stopping date and moneyness per path, stays scalar for its registers)
     auto exercise = [&](int d, float b0, float b1, float b2, float b3) {
         const float *sl = sm.S[d % kSlots];
+        if (GREEKS) {
 #pragma unroll
-        for (int i = 0; i < kPPT; ++i) {
-            const float y = sl[w + i * kWorkers];
-            const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
-            const float h = PUT ? -y : y;
-            const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
-            cf[i] = ex ? h : cf[i];
-            if (GREEKS) {
+            for (int i = 0; i < kPPT; ++i) {
+                const float y = sl[pidx(i)];
+                const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+                const float h = PUT ? -y : y;
+                const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
+                cf[i] = ex ? h : cf[i];
                 tau[i] = ex ? d : tau[i];
                 yt[i] = ex ? y : yt[i];
+            }
+            return;
+        }
+        const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
+#pragma unroll
+        for (int i = 0; i < kPPT; i += 2) {
+            const f2 Y = *reinterpret_cast<const f2 *>(sl + pidx(i));
+            const f2 C = f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0);
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const float y = h2 ? f2_hi(Y) : f2_lo(Y);
+                const float cont = h2 ? f2_hi(C) : f2_lo(C);
+                const float h = PUT ? -y : y;
+                const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
+                cf[i + h2] = ex ? h : cf[i + h2];
             }
         }
     };
@@ -436,16 +463,37 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             }
             float rr[4] = {0.f, 0.f, 0.f, 0.f};
             const float *sl = sm.S[j % kSlots];
+            if (GREEKS) {
 #pragma unroll
-            for (int i = 0; i < kPPT; ++i) {
-                cf[i] *= disc;
-                const float y = sl[w + i * kWorkers];
-                const float c = y != 0.f ? cf[i] : 0.f;
-                const float y2 = y * y;
-                rr[0] += c;
-                rr[1] = fmaf(c, y, rr[1]);
-                rr[2] = fmaf(c, y2, rr[2]);
-                rr[3] = fmaf(c, y2 * y, rr[3]);
+                for (int i = 0; i < kPPT; ++i) {
+                    cf[i] *= disc;
+                    const float y = sl[pidx(i)];
+                    const float c = y != 0.f ? cf[i] : 0.f;
+                    const float yy = y * y;
+                    rr[0] += c;
+                    rr[1] = fmaf(c, y, rr[1]);
+                    rr[2] = fmaf(c, yy, rr[2]);
+                    rr[3] = fmaf(c, yy * y, rr[3]);
+                }
+            } else {
+                const f2 z2 = f2_splat(0.f), DISC = f2_splat(disc);
+                f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
+#pragma unroll
+                for (int i = 0; i < kPPT; i += 2) {
+                    const f2 Y = *reinterpret_cast<const f2 *>(sl + pidx(i));
+                    const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
+                    cf[i] = f2_lo(C);
+                    cf[i + 1] = f2_hi(C);
+                    R0 = f2_add(R0, f2_pack(f2_lo(Y) != 0.f ? cf[i] : 0.f, f2_hi(Y) != 0.f ? cf[i + 1] : 0.f));
+                    const f2 YY = f2_mul(Y, Y);
+                    R1 = f2_fma(C, Y, R1);                        // y = 0 off the money
+                    R2 = f2_fma(C, YY, R2);
+                    R3 = f2_fma(C, f2_mul(YY, Y), R3);
+                }
+                rr[0] = f2_lo(R0) + f2_hi(R0);
+                rr[1] = f2_lo(R1) + f2_hi(R1);
+                rr[2] = f2_lo(R2) + f2_hi(R2);
+                rr[3] = f2_lo(R3) + f2_hi(R3);
             }
             const float r = warp_sum4(rr, lane);
             const int k = (lane >> 3) & 3;
@@ -579,7 +627,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     const float mu = r - 0.5f * sig * sig;
 #pragma unroll
     for (int i = 0; i < kPPT; ++i) {
-        if (w + i * kWorkers >= nloc) continue;
+        if (pidx(i) >= nloc) continue;
         fs[0] += cf[i];
         fs[1] += cf[i] * cf[i];
         if (GREEKS && cf[i] > 0.f) {
