@@ -1,23 +1,25 @@
 // Mixed-precision Longstaff-Schwartz sweep for sm_103a (ref. [12]; the
 // backward induction of §V), built around the per-date latency chain.
 //
-// One CTA of 1024 threads per SM: warp 0 is the solver, warps 1..31 own
-// 8 paths per thread (7936 paths per CTA, a contiguous slice of every date
-// row).  Per CTA:
+// One CTA of 1024 threads per SM: warps 0 and 1 are solvers, warps 2..31
+// own 8 paths per thread (7680 paths per CTA, a contiguous slice of every
+// date row).  Per CTA:
 //   - a ring of 5 date slices in shared memory, filled by TMA bulk copies
 //     (cp.async.bulk + mbarrier) up to 5 dates ahead of use, so HBM latency
 //     never sits on the critical path;
 //   - the in-the-money Gram moments M_k = sum y^k (y = S/K - 1) depend on
 //     the paths only, so they are summed from the ring and exchanged two
-//     dates before they are needed; the solver warp turns each date's
-//     totals into the inverse Gram matrix in FP64 (16 cofactors in
-//     parallel; the degenerate-date test on the equilibrated Cholesky
-//     pivots is decided from leading principal minors) while the path
-//     warps work on later dates;
-//   - what is left on the critical path per date: CF *= e^{-r dt}, the
-//     right-hand sides R_k = sum y^k CF, a warp-shuffle + double-float block
-//     sum, the cross-CTA exchange, beta = Ginv R in FP64 (16 lanes) and the
-//     exercise update h > phi(y).beta.
+//     dates before they are needed; the solver warps (alternate dates) turn
+//     each date's totals into the inverse Gram matrix in FP64 (16 cofactors
+//     in parallel; the degenerate-date test on the equilibrated Cholesky
+//     pivots is decided from leading principal minors) while the path warps
+//     work on later dates;
+//   - what is left on the critical path per date: the exercise update
+//     h > phi(y).beta of the previous date, CF *= e^{-r dt} and the
+//     right-hand sides R_k = sum y^k CF (packed f32x2 on path pairs), a
+//     warp-shuffle + double-float block sum, the cross-CTA exchange (whose
+//     latency the Gram pass of a later date fills), and beta = Ginv R in
+//     double-float, formed by every path warp itself.
 // Cross-CTA exchange: every CTA writes its partial of each value as one
 // 64-bit unit (FP32 payload, 32-bit tag = launch epoch and exchange index)
 // and every CTA polls all units of that value until every tag matches, then
@@ -60,11 +62,10 @@ struct SmemV2 {
     double gtot[3][8];              // Gram totals by date mod 3
     double ginv[3][16];             // inverse Gram matrix (FP64) by date mod 3
     float ginv_hi[3][16], ginv_lo[3][16];  // the same as double-float for the path warps
-    float beta[4];
+    float betaw[32][4];             // per-warp copy of beta (Greeks variant: fewer registers)
     double sA[kSolvers][16];
     double sP[kSolvers][4];
     int gdeg[3];
-    int deg_cur;                    // degenerate flag of the coefficients in beta
     int pend[kSlots];
     volatile int gtot_date[3];      // date whose Gram totals are in gtot[b]
     volatile int ginv_date[3];      // date whose inverse is in ginv*[b]
@@ -269,8 +270,6 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             sm.gtot_date[b] = 0;
             sm.ginv_date[b] = 0;
         }
-        sm.deg_cur = 0;
-        for (int k = 0; k < 4; ++k) sm.beta[k] = 0.f;
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -394,7 +393,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         for (int d = m; d >= 1 && d > m - kSlots; --d) issue(d);
 
     float cf[kPPT];
-    int tau[GREEKS ? kPPT : 1];
+    uint32_t tau2[GREEKS ? kPPT / 2 : 1];    // stopping dates, two 16-bit halves per word
     float yt[GREEKS ? kPPT : 1];
     int degenerate = 0;
     const bool ok = wait_slice(m);
@@ -406,7 +405,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             const float y = fmaf(sl[idx], invK, -1.f);
             const float h = PUT ? -y : y;
             cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
-            if (GREEKS) { tau[i] = m; yt[i] = y; }
+            if (GREEKS) {
+                if ((i & 1) == 0) tau2[i >> 1] = (uint32_t)m * 0x10001u;
+                yt[i] = y;
+            }
         }
     }
     bool stop = bar_work_any(!ok || sm.abort);
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // Gram moments of date m-1, posted at the first exchange (index m+1)
     if (m >= 2 && !stop && wait_slice(m - 1)) gram_post(m - 1, (m + 1) & 1);
 
-    // exercise at date d with the coefficients in sm.beta
+    // exercise at date d with the coefficients b0..b3
     // (packed f32x2 pairs; the Greeks variant, which also carries the
     // stopping date and moneyness per path, stays scalar for its registers)
     auto exercise = [&](int d, float b0, float b1, float b2, float b3) {
@@ -427,7 +429,8 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 const float h = PUT ? -y : y;
                 const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
                 cf[i] = ex ? h : cf[i];
-                tau[i] = ex ? d : tau[i];
+                if (ex) tau2[i >> 1] = (i & 1) ? ((tau2[i >> 1] & 0xffffu) | ((uint32_t)d << 16))
+                                               : ((tau2[i >> 1] & 0xffff0000u) | (uint32_t)d);
                 yt[i] = ex ? y : yt[i];
             }
             return;
@@ -448,6 +451,12 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         }
     };
 
+    // coefficients of the latest exchange and their degenerate flag, formed
+    // by every path warp itself from the shared totals and inverse
+    float bet[GREEKS ? 1 : 4] = {};
+    int deg_cur = 0;
+    if (GREEKS && lane < 4) sm.betaw[warp][lane] = 0.f;
+    auto beta_k = [&](int k) { return GREEKS ? sm.betaw[warp][k] : bet[GREEKS ? 0 : k]; };
     for (int j = m + 1; j >= 1 && !stop; --j) {
         const bool hasR = j <= m - 1;
         const bool hasG = j - 2 >= 1;
@@ -455,10 +464,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             // exercise at j+1 (coefficients of the previous exchange), then
             // discount to t_j and sum the right-hand sides of date j
             if (j + 1 <= m - 1) {
-                if (sm.deg_cur) {
+                if (deg_cur) {
                     if (w == 0) ++degenerate;
                 } else {
-                    exercise(j + 1, sm.beta[0], sm.beta[1], sm.beta[2], sm.beta[3]);
+                    exercise(j + 1, beta_k(0), beta_k(1), beta_k(2), beta_k(3));
                 }
             }
             float rr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -500,7 +509,8 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             if ((lane & 7) == 0 && k < p) sm.redR[warp][k] = r;
         }
         const uint32_t mask = (hasG ? ((1u << nmom) - 1u) : 0u) | (hasR ? (((1u << p) - 1u) << 7) : 0u);
-        bar_work();                                               // B1
+        stop = bar_work_any(sm.abort);                            // B1
+        if (stop) break;
         if (w == 0 && j + 1 <= m - 1 && j + 1 - kSlots >= 1) issue(j + 1 - kSlots);   // slice j+1 consumed
         // cross-CTA exchange: warp kXW0+k owns value slot k; it posts, runs
         // its share of the next Gram pass (which also absorbs the other
@@ -564,43 +574,50 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             if (lane == 0) sm.gtot_date[b] = j - 2;
         }
         if (hasR) {
-            if (warp == kXW0) {
-                const int b = j % 3;
-                const uint64_t t0 = globaltimer();
-                bool bail = false;
-                while (sm.ginv_date[b] != j) {
-                    if (sm.abort || globaltimer() - t0 > timeout_ns) {
-                        bail = true;
-                        break;
-                    }
+            // beta_j = Ginv_j R_j in double-float, in every path warp: lane
+            // 4k+l one product, two butterfly steps, then beta_k from lane 4k
+            const int b = j % 3;
+            const uint64_t t0 = globaltimer();
+            bool bail = false;
+            while (sm.ginv_date[b] != j) {
+                if (sm.abort || globaltimer() - t0 > timeout_ns) {
+                    bail = true;
+                    break;
                 }
-                if (bail && lane == 0) {
+            }
+            if (__any_sync(kFull, bail)) {
+                if (lane == 0) {
                     atomicCAS(status, 0, AMC_ETIMEOUT);
                     sm.abort = 1;
                 }
+            } else {
                 __threadfence_block();
-                // beta_k = sum_l Ginv_kl R_l in double-float: lane 4k+l one product,
-                // then two butterfly steps
                 const int bl = lane & 3;
                 dfl t = {0.f, 0.f};
                 if (lane < 16 && bl < p)
-                    t = df_mul(dfl{sm.ginv_hi[b][lane], sm.ginv_lo[b][lane]},
+                    t = df_mul(dfl{sm.ginv_hi[b][lane & 15], sm.ginv_lo[b][lane & 15]},
                                dfl{sm.tot_hi[7 + bl], sm.tot_lo[7 + bl]});
                 t = df_add(t, df_shfl_xor(t, 1));
                 t = df_add(t, df_shfl_xor(t, 2));
-                if (lane < 16 && bl == 0) sm.beta[lane >> 2] = __fadd_rn(t.hi, t.lo);
-                if (lane == 0) sm.deg_cur = sm.gdeg[b];
+                const float bk = __fadd_rn(t.hi, t.lo);
+                if (GREEKS) {
+                    if (lane < 16 && bl == 0) sm.betaw[warp][lane >> 2] = bk;
+                    __syncwarp();
+                } else {
+#pragma unroll
+                    for (int k = 0; k < (GREEKS ? 1 : 4); ++k) bet[k] = __shfl_sync(kFull, bk, 4 * k);
+                }
+                deg_cur = sm.gdeg[b];
             }
-            stop = bar_work_any(sm.abort);                        // B3
-            if (stop) break;
         }
     }
-    // the last exercise date, t_1
+    // the last exercise date, t_1 (a failed wait for its coefficients shows in sm.abort)
+    if (!stop) stop = bar_work_any(sm.abort);
     if (!stop && m >= 2) {
-        if (sm.deg_cur) {
+        if (deg_cur) {
             if (w == 0) ++degenerate;
         } else {
-            exercise(1, sm.beta[0], sm.beta[1], sm.beta[2], sm.beta[3]);
+            exercise(1, beta_k(0), beta_k(1), beta_k(2), beta_k(3));
         }
     }
 
@@ -632,7 +649,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         fs[1] += cf[i] * cf[i];
         if (GREEKS && cf[i] > 0.f) {
             const float St = Kf * (1.f + yt[i]);
-            const float t = (float)tau[i] * dt;
+            const float t = (float)((tau2[i >> 1] >> (16 * (i & 1))) & 0xffffu) * dt;
             const float dfac = expf(-r * t);
             const float dh = PUT ? -1.f : 1.f;
             const float Wt = (logf(St / S0) - mu * t) / sig;
