@@ -64,7 +64,9 @@ def _lib():
         lib.orc_bs.restype = ctypes.c_double
         lib.orc_solve_normal.argtypes = [ctypes.c_int, _dp, _dp, _dp]
         lib.orc_lsm.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _i32p, _dp, _i64p]
+                                ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _i32p, _dp, _i64p, _i32p]
+        lib.orc_value_boundary.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _i32p, _dp, _i32p]
         lib.orc_paper_ub.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
         lib.orc_european.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
         lib.orc_pathwise_greeks.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 5 +
@@ -190,14 +192,46 @@ def lsm(S, type_, K, r, T, p, details=False):
     tau = np.zeros(N, dtype=np.int32) if details else None
     cf = np.zeros(N) if details else None
     nitm = np.zeros(m, dtype=np.int64) if details else None
+    deg = np.zeros(m, dtype=np.int32) if details else None
     rc = _lib().orc_lsm(type_, K, r, T, m, N, p, _ptr(S, _dp), _ptr(out, _dp), _ptr(beta, _dp),
-                        _ptr(tau, _i32p), _ptr(cf, _dp), _ptr(nitm, _i64p))
+                        _ptr(tau, _i32p), _ptr(cf, _dp), _ptr(nitm, _i64p), _ptr(deg, _i32p))
     if rc != 0:
         raise ValueError("oracle lsm failed")
     res = {"price": out[0], "std_err": out[1], "degenerate_dates": int(out[2])}
     if details:
-        res.update(beta=beta, tau=tau, cf=cf, n_itm=nitm)
+        res.update(beta=beta, tau=tau, cf=cf, n_itm=nitm, deg=deg)
     return res
+
+
+def value_boundary(S, type_, K, r, T, beta, deg, details=False):
+    """Value the paths S with a given exercise boundary: beta[m, p] in
+    currency units on the basis (1, y, .., y^(p-1)), y = S/K - 1; deg[m]
+    nonzero = no exercise at that date."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    deg = np.ascontiguousarray(deg, dtype=np.int32)
+    m, N = S.shape
+    p = beta.shape[1]
+    out = np.zeros(3)
+    tau = np.zeros(N, dtype=np.int32) if details else None
+    rc = _lib().orc_value_boundary(type_, K, r, T, m, N, p, _ptr(S, _dp), _ptr(beta, _dp), _ptr(deg, _i32p),
+                                   _ptr(out, _dp), _ptr(tau, _i32p))
+    if rc != 0:
+        raise ValueError("oracle value_boundary failed")
+    res = {"price": out[0], "std_err": out[1], "degenerate_dates": int(out[2])}
+    if details:
+        res["tau"] = tau
+    return res
+
+
+def price_oos(S0, K, r, sigma, T, n_steps, n_paths, basis=3, type=PUT, seed=0, value_seed=1):
+    """Out-of-sample LSM: boundary fitted on the points of `seed`, applied to
+    the independent points of `value_seed`.  Returns (fit result with beta
+    and deg, valuation result)."""
+    fit = lsm(paths(S0, r, sigma, T, n_steps, n_paths, seed), type, K, r, T, basis, details=True)
+    val = value_boundary(paths(S0, r, sigma, T, n_steps, n_paths, value_seed), type, K, r, T, fit["beta"],
+                         fit["deg"])
+    return fit, val
 
 
 def paper_ub(S, type_, S0, K, r, sigma, T):

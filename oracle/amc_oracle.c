@@ -366,10 +366,11 @@ int orc_solve_normal(int p, const double *G, const double *b, double *beta)
  *       then CF_i = h(S_{i,j}), tau_i = j;
  *   price = e^{-r dt} mean(CF),  std_err = e^{-r dt} sd(CF) / sqrt(N).
  * Outputs (all optional): beta[(j-1)*p + k] (zeros on degenerate dates and at
- * j = m), tau[i], cf[i] (CF at t_1, undiscounted to 0), n_itm[j-1].        */
+ * j = m), tau[i], cf[i] (CF at t_1, undiscounted to 0), n_itm[j-1],
+ * deg[j-1] (1 on degenerate dates and at j = m, else 0).                   */
 int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
             const double *S, double *out /* price, std_err, degenerate */,
-            double *beta_out, int32_t *tau_out, double *cf_out, int64_t *nitm_out)
+            double *beta_out, int32_t *tau_out, double *cf_out, int64_t *nitm_out, int32_t *deg_out)
 {
     double dt = T / m, disc = exp(-r * dt);
     double *CF = (double *)malloc(sizeof(double) * (size_t)N);
@@ -377,6 +378,7 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
     int degenerate = 0;
     if (!CF || !tau || p < 1 || p > 8) { free(CF); free(tau); return -1; }
     if (beta_out) memset(beta_out, 0, sizeof(double) * (size_t)(m * p));
+    if (deg_out) for (int j = 0; j < m; ++j) deg_out[j] = 1;
     for (int64_t i = 0; i < N; ++i) {
         CF[i] = orc_payoff(type, S[(int64_t)(m - 1) * N + i], K);
         tau[i] = m;
@@ -412,6 +414,7 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
         }
         if (beta_out)
             for (int k = 0; k < p; ++k) beta_out[(j - 1) * p + k] = beta[k];
+        if (deg_out) deg_out[j - 1] = 0;
         for (int64_t i = 0; i < N; ++i) {
             double h = orc_payoff(type, Sj[i], K);
             if (!(h > 0.0)) continue;
@@ -430,6 +433,57 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
     if (tau_out) memcpy(tau_out, tau, sizeof(int32_t) * (size_t)N);
     if (cf_out) memcpy(cf_out, CF, sizeof(double) * (size_t)N);
     free(CF); free(tau);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Valuation with a given exercise boundary (a second Longstaff-Schwartz
+ * pass; ref. [12] values out of sample, the paper in sample).  The
+ * boundary is the continuation value c_j(y) = sum_k beta[(j-1)*p+k] y^k
+ * (currency units, y = S/K - 1) of each date j with deg[j-1] == 0; dates
+ * with deg[j-1] != 0 have no exercise.  On each path, the same recursion as
+ * the in-sample sweep without its regression:
+ *   CF = h(S_m), tau = m;
+ *   for j = m-1 .. 1: CF <- CF e^{-r dt};
+ *                     if deg[j-1] == 0 and h(S_j) > 0 and h(S_j) > c_j(y_j):
+ *                         CF = h(S_j), tau = j;
+ *   price = e^{-r dt} mean(CF),  std_err = e^{-r dt} sd(CF) / sqrt(N).
+ * With the coefficients fitted on these same paths it repeats the in-sample
+ * decisions; on paths independent of the fit it is a low-biased estimator
+ * of the Bermudan value (any stopping rule is at most optimal).           */
+int orc_value_boundary(int type, double K, double r, double T, int m, int64_t N, int p, const double *S,
+                       const double *beta, const int32_t *deg, double *out, int32_t *tau_out)
+{
+    double dt = T / m, disc = exp(-r * dt);
+    double *CF = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!CF || p < 1 || p > 8) { free(CF); return -1; }
+    int degenerate = 0;
+    for (int j = 1; j < m; ++j) degenerate += deg[j - 1] != 0;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double cf = orc_payoff(type, S[(int64_t)(m - 1) * N + i], K);
+        int32_t tau = m;
+        for (int j = m - 1; j >= 1; --j) {
+            cf *= disc;
+            if (deg[j - 1]) continue;
+            double s = S[(int64_t)(j - 1) * N + i];
+            double h = orc_payoff(type, s, K);
+            if (!(h > 0.0)) continue;
+            double y = s / K - 1.0, c = 0.0, yk = 1.0;
+            for (int k = 0; k < p; ++k) { c += beta[(j - 1) * p + k] * yk; yk *= y; }
+            if (h > c) { cf = h; tau = j; }
+        }
+        CF[i] = cf;
+        if (tau_out) tau_out[i] = tau;
+    }
+    double sum = 0.0, sum2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) sum += CF[i];
+    double mean = sum / (double)N;
+    for (int64_t i = 0; i < N; ++i) sum2 += (CF[i] - mean) * (CF[i] - mean);
+    out[0] = disc * mean;
+    out[1] = N > 1 ? disc * sqrt(sum2 / (double)(N - 1)) / sqrt((double)N) : 0.0;
+    out[2] = (double)degenerate;
+    free(CF);
     return 0;
 }
 

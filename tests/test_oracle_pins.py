@@ -334,3 +334,50 @@ def test_lsm_pathwise_greeks_vs_central_differences():
     assert abs(g["vega"] - fd_vega) < 0.05 * abs(fd_vega) + 0.2
     base = oracle.price(S0, K, r, sigma, T, m, N, basis=3, seed=5)["price"]
     assert abs(g["price"] - base) < 1e-12
+
+
+# ------------------------------------------------ boundary valuation (second pass)
+def _fit(seed, m=50, n=2 ** 13, p=3):
+    S = oracle.paths(36.0, .06, .2, 1.0, m, n, seed)
+    return S, oracle.lsm(S, oracle.PUT, 40.0, .06, 1.0, p, details=True)
+
+
+def test_boundary_valuation_on_fitting_paths_repeats_in_sample_decisions():
+    S, fit = _fit(1)
+    val = oracle.value_boundary(S, oracle.PUT, 40.0, .06, 1.0, fit["beta"], fit["deg"], details=True)
+    assert val["price"] == fit["price"] and val["std_err"] == fit["std_err"]
+    assert np.array_equal(val["tau"], fit["tau"])
+    assert val["degenerate_dates"] == fit["degenerate_dates"]
+
+
+def test_boundary_without_exercise_is_the_european_estimator():
+    S, fit = _fit(2)
+    m = S.shape[0]
+    val = oracle.value_boundary(S, oracle.PUT, 40.0, .06, 1.0, fit["beta"], np.ones(m, dtype=np.int32))
+    eu = oracle.european(S, oracle.PUT, 40.0, .06, 1.0)
+    assert val["price"] == pytest.approx(eu["price"], rel=1e-13)
+    assert val["degenerate_dates"] == m - 1
+
+
+def test_boundary_exercise_whenever_in_the_money_is_first_hitting_time():
+    m, n, K, r, T = 12, 4096, 40.0, .06, 1.0
+    S = oracle.paths(36.0, r, .2, T, m, n, 3)
+    beta = np.zeros((m, 3))
+    beta[:, 0] = -1e300                      # continuation below any positive payoff
+    val = oracle.value_boundary(S, oracle.PUT, K, r, T, beta, np.zeros(m, dtype=np.int32), details=True)
+    h = np.maximum(K - S, 0.0)               # [m, n]
+    itm = h[:-1] > 0.0
+    first = np.where(itm.any(axis=0), itm.argmax(axis=0) + 1, m)    # first in-the-money date, else maturity
+    t = first * (T / m)
+    ref = np.mean(h[first - 1, np.arange(n)] * np.exp(-r * t))
+    assert np.array_equal(val["tau"], first)
+    assert val["price"] == pytest.approx(ref, rel=1e-12)
+
+
+def test_out_of_sample_price_is_low_biased_against_the_bermudan_tree():
+    fit, val = oracle.price_oos(36.0, 40.0, .06, .2, 1.0, 50, 2 ** 14, basis=3, type=oracle.PUT, seed=1,
+                                value_seed=2)
+    tree = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000, 50, bermudan=True)
+    assert val["price"] <= tree + 3.0 * val["std_err"]
+    assert val["price"] >= tree - 0.01 * tree
+    assert val["price"] > oracle.bs(oracle.PUT, 36.0, 40.0, .06, .2, 1.0)
