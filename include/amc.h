@@ -85,6 +85,11 @@ typedef struct amc_result {
 /* Device result block written by the asynchronous calls: 8 doubles,
  * [price, std_err, delta, vega, degenerate_dates, status, 0, 0].           */
 #define AMC_RES_DOUBLES 8
+/* Exercise boundary of one LSM option: AMC_COEF_STRIDE doubles per date
+ * d = 1..m (row d-1): c_0..c_3, the continuation value divided by K as a
+ * polynomial in the moneyness y = S/K - 1 (c_k = 0 for k >= basis), then a
+ * degenerate flag (nonzero: no exercise at d; always set for d = m).       */
+#define AMC_COEF_STRIDE 5
 
 typedef struct amc_ctx amc_ctx;
 
@@ -154,6 +159,26 @@ int amc_sweep(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
 int amc_price_device(amc_ctx *ctx, const amc_option *opt, int prec, void *S_dev,
                      int64_t ld, double *res_dev, void *stream);
 
+/* Second Longstaff-Schwartz pass (ref. [12]; the paper values in sample,
+ * with the paths it regresses on).  amc_fit_boundary runs the LSM sweep of
+ * an AMC_RULE_LSM option on S (as amc_sweep, in-sample result into
+ * res_dev) and also writes the fitted boundary into
+ * coef_dev[n_steps * AMC_COEF_STRIDE].  amc_value_boundary values the paths
+ * S with a given boundary and no regression: on each path CF = h(S_m), then
+ * for d = m-1..1, CF <- CF e^{-r dt} and CF = h(S_d) if d is not degenerate,
+ * S_d is in the money and h(S_d) > K c_d(y_d); price = e^{-r dt} mean CF
+ * (result block as amc_sweep, delta and vega 0, degenerate_dates = flagged
+ * dates).  With paths independent of those the boundary was fitted on, this
+ * is a low-biased estimator of the Bermudan value; with the fitting paths
+ * it repeats the in-sample exercise decisions.  One streaming read of S,
+ * no reduction across the grid.  Both asynchronous; S, ld as amc_sweep;
+ * coef_dev 8-byte aligned device memory (AMC_EINVAL otherwise, or if the
+ * option's rule is not AMC_RULE_LSM).                                      */
+int amc_fit_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
+                     int64_t ld, double *coef_dev, double *res_dev, void *stream);
+int amc_value_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
+                       int64_t ld, const double *coef_dev, double *res_dev, void *stream);
+
 /* --------------------------------------------------- host-level calls */
 /* Price one option (paths in the context arena), blocking; out on host.   */
 int amc_price_american(amc_ctx *ctx, double S0, double K, double r, double sigma,
@@ -165,6 +190,12 @@ int amc_price_american(amc_ctx *ctx, double S0, double K, double r, double sigma
  * launch.  Blocking; out[n] on host.                                       */
 int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                     amc_result *out);
+/* Out-of-sample LSM price (paths in the context arena), blocking: the
+ * boundary is fitted on the points of opt->seed (in-sample result into
+ * fit, may be null) and applied to the independent points of value_seed
+ * (result into value).                                                     */
+int amc_price_oos(amc_ctx *ctx, const amc_option *opt, uint64_t value_seed, int prec,
+                  amc_result *fit, amc_result *value);
 /* Price, delta and vega of n options (frozen-boundary pathwise adjoint).   */
 int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                double *price, double *delta, double *vega);

@@ -22,6 +22,7 @@ AMC_PUT, AMC_CALL = 0, 1
 AMC_RULE_LSM, AMC_RULE_PAPER_UB, AMC_RULE_EUROPEAN = 0, 1, 2
 AMC_FP64, AMC_MIXED = 0, 1
 AMC_RES_DOUBLES = 8
+AMC_COEF_STRIDE = 5
 AMC_MAX_STEPS = 512
 
 
@@ -84,6 +85,9 @@ SIGNATURES = {
     "amc_generate_paths": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp]),
     "amc_sweep": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "amc_price_device": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "amc_fit_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
+    "amc_value_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
+    "amc_price_oos": (ctypes.c_int, [_vp, _optp, _u64, ctypes.c_int, _resp, _resp]),
     "amc_price_american": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _u64,
                                           ctypes.c_int, ctypes.c_int, _resp]),
@@ -270,6 +274,30 @@ def amc_price_device(ctx, opt, prec, S, res, ld=None, stream=None):
     ld = S.shape[1] if ld is None else ld
     _check(lib().amc_price_device(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(res),
                                   _stream(stream)), "amc_price_device")
+
+
+def amc_fit_boundary(ctx, opt, prec, S, coef, res, ld=None, stream=None):
+    """LSM sweep on S that also writes the fitted boundary into coef
+    (device, [n_steps, AMC_COEF_STRIDE] doubles)."""
+    ld = S.shape[1] if ld is None else ld
+    _check(lib().amc_fit_boundary(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(coef),
+                                  _ptr(res), _stream(stream)), "amc_fit_boundary")
+
+
+def amc_value_boundary(ctx, opt, prec, S, coef, res, ld=None, stream=None):
+    """Value the paths S with the boundary coef (no regression)."""
+    ld = S.shape[1] if ld is None else ld
+    _check(lib().amc_value_boundary(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(coef),
+                                    _ptr(res), _stream(stream)), "amc_value_boundary")
+
+
+def amc_price_oos(ctx, opt, value_seed, prec=AMC_MIXED):
+    """Out-of-sample price: boundary fitted on opt's points, applied to the
+    points of value_seed.  Returns (fit result, value result) dicts."""
+    fit, val = amc_result(), amc_result()
+    _check(lib().amc_price_oos(ctx.handle, ctypes.byref(make_option(opt)), value_seed, prec, ctypes.byref(fit),
+                               ctypes.byref(val)), "amc_price_oos")
+    return _res_dict(fit), _res_dict(val)
 
 
 # ------------------------------------------------------------ serving

@@ -83,9 +83,12 @@ struct Job {
     void *fin;                      // [n_cta][4] final per-CTA sums
     double *res;                    // [AMC_RES_DOUBLES]
     int32_t *status;                // shared error word of the launch
+    double *coef;                   // exercise boundary [m][kCoefStride] written by an LSM sweep / read by valuation, or null
     uint64_t *xch;                  // tagged exchange units [m+2][kXV][n_cta] (mixed LSM sweep)
 };
 
+constexpr int kCoefStride = AMC_COEF_STRIDE;   // c_0..c_3 (units of K, basis y^k), degenerate flag
+constexpr int kValueThreads = 256;             // boundary valuation: threads per CTA, 8 paths per thread
 constexpr int kNV = 12;             // cross-CTA values per date: 2p-1 moments + p RHS (p <= 4)
 
 // Mixed-precision LSM sweep (sweep_v2.cu): 2 solver warps + 30 path warps,
@@ -131,6 +134,7 @@ cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bo
                                   cudaStream_t st);
 cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
+cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStream_t st);
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 

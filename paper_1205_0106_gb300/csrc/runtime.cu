@@ -152,7 +152,7 @@ int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, 
 }
 
 int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, bool greeks, double *res,
-             cudaStream_t st) {
+             cudaStream_t st, double *coef = nullptr) {
     AMC_TRY(host_validate(o));
     AMC_TRY(check_prec(prec));
     AMC_TRY(check_storage(S, ld, o->n_paths));
@@ -177,6 +177,7 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     J.res = res;
     J.status = c->status1;
     J.xch = c->xch1;
+    J.coef = coef;
     if (c->inject_kind == 1) {
         J.inject_date = (int32_t)c->inject_arg;
         c->inject_kind = 0;
@@ -191,6 +192,35 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     return launch_sweeps(c, a, pl, pl.ctas, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st);
 }
 
+
+// Valuation of caller paths with a given boundary (one streaming launch and
+// its finalize; the grid covers 8 paths per thread, at most gcap CTAs).
+int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, const double *coef, double *res,
+             cudaStream_t st) {
+    AMC_TRY(host_validate(o));
+    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_storage(S, ld, o->n_paths));
+    if (o->rule != AMC_RULE_LSM || !coef || ((uintptr_t)coef & 7u) != 0 || !res || ((uintptr_t)res & 7u) != 0)
+        return AMC_EINVAL;
+    KArgs &a = c->args;
+    memset(&a, 0, sizeof(KArgs));
+    Job &J = a.one;
+    fill_job_common(o, &J);
+    J.S = const_cast<void *>(S);
+    J.ld = ld;
+    J.coef = const_cast<double *>(coef);
+    const int64_t units = (o->n_paths + 8LL * kValueThreads - 1) / (8LL * kValueThreads);
+    J.n_cta = (int)std::min<int64_t>(units, c->gcap);
+    J.fin = c->fin1;
+    J.res = res;
+    J.status = c->status1;
+    a.n_jobs = 1;
+    a.max_m = o->n_steps;
+    AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
+    AMC_TRY_CUDA(launch_value_boundary(a, J.n_cta, prec == AMC_FP64, st));
+    AMC_TRY_CUDA(launch_finalize(a, st));
+    return AMC_OK;
+}
 
 amc_option make_option(double S0, double K, double r, double sigma, double T, int n_steps, int64_t n_paths,
                        int basis, int type, uint64_t seed, int rule) {
@@ -631,6 +661,53 @@ int amc_price_device(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, i
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     AMC_TRY(do_generate(c, opt, prec, S_dev, ld, (cudaStream_t)stream));
     return do_sweep(c, opt, prec, S_dev, ld, false, res_dev, (cudaStream_t)stream);
+}
+
+int amc_fit_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, double *coef_dev,
+                     double *res_dev, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt || opt->rule != AMC_RULE_LSM || !coef_dev || ((uintptr_t)coef_dev & 7u) != 0) return AMC_EINVAL;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    return do_sweep(c, opt, prec, S_dev, ld, false, res_dev, (cudaStream_t)stream, coef_dev);
+}
+
+int amc_value_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld,
+                       const double *coef_dev, double *res_dev, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt) return AMC_EINVAL;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    return do_value(c, opt, prec, S_dev, ld, coef_dev, res_dev, (cudaStream_t)stream);
+}
+
+int amc_price_oos(amc_ctx *c, const amc_option *opt, uint64_t value_seed, int prec, amc_result *fit,
+                  amc_result *value) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt || !value || opt->rule != AMC_RULE_LSM) return AMC_EINVAL;
+    AMC_TRY(host_validate(opt));
+    AMC_TRY(check_prec(prec));
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    c->arena_top = 0;
+    const int64_t ld = host_ld(opt->n_paths);
+    void *S;
+    double *coef, *res2;
+    AMC_TRY(arena_alloc(c, (size_t)opt->n_steps * ld * (prec == AMC_FP64 ? 8 : 4), &S));
+    AMC_TRY(arena_alloc(c, sizeof(double) * kCoefStride * opt->n_steps, (void **)&coef));
+    AMC_TRY(arena_alloc(c, sizeof(double) * 2 * AMC_RES_DOUBLES, (void **)&res2));
+    cudaStream_t st = c->stream;
+    amc_option ov = *opt;
+    ov.seed = value_seed;
+    AMC_TRY(do_generate(c, opt, prec, S, ld, st));
+    AMC_TRY(do_sweep(c, opt, prec, S, ld, false, res2, st, coef));
+    AMC_TRY(do_generate(c, &ov, prec, S, ld, st));
+    AMC_TRY(do_value(c, &ov, prec, S, ld, coef, res2 + AMC_RES_DOUBLES, st));
+    double h[2 * AMC_RES_DOUBLES];
+    AMC_TRY_CUDA(cudaMemcpyAsync(h, res2, sizeof(h), cudaMemcpyDeviceToHost, st));
+    AMC_TRY_CUDA(cudaStreamSynchronize(st));
+    int s1 = AMC_OK;
+    if (fit) s1 = result_from(h, fit);
+    else if ((int32_t)h[5] != 0) s1 = (int32_t)h[5];
+    int s2 = result_from(h + AMC_RES_DOUBLES, value);
+    return s1 != AMC_OK ? s1 : s2;
 }
 
 int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, double T, int n_steps,

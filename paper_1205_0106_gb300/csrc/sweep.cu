@@ -274,6 +274,8 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
         }
     }
     int degenerate = 0;
+    if (J.coef && lc == 0 && tid < kCoefStride)             // maturity: no exercise decision
+        J.coef[(size_t)(m - 1) * kCoefStride + tid] = tid == 4 ? 1.0 : 0.0;
     for (int j = m - 1; j >= 1; --j) {
         const Real *row = S + (int64_t)(j - 1) * ld;
         Real s[P];
@@ -365,6 +367,11 @@ sweep_lsm_kernel(const __grid_constant__ KArgs a) {
             bool ok = s_tot[0] >= (double)p && solve_normal(p, s_tot, s_tot + 7, beta);
             for (int k = 0; k < 4; ++k) s_beta[k] = beta[k];
             s_flag = ok ? 0 : 2;
+            if (J.coef && lc == 0) {                          // fitted boundary of date j (units of K)
+                double *cj = J.coef + (size_t)(j - 1) * kCoefStride;
+                for (int k = 0; k < 4; ++k) cj[k] = ok ? beta[k] * J.invK : 0.0;
+                cj[4] = ok ? 0.0 : 1.0;
+            }
         }
         __syncthreads();
         if (s_flag == 2) {
