@@ -12,7 +12,8 @@ L2, so every step streams it from HBM.
 Keys beyond the base contract: fp64 (the same step in all-FP64 on the GPU),
 err_vs_oracle (|price - FP64 oracle price| on identical points, in units of
 K), roofline (dominant kernel) and roofline_sweep, cpu_baseline (the oracle
-on a bounded sample, host cores), clocks, serving (a Poisson request replay),
+on a bounded sample, host cores), clocks, oos (the second, out-of-sample
+pass: the boundary valuation kernel and its HBM roofline), serving (a Poisson request replay),
 batch and greeks (the 4096-option batch and 1024-option Greeks workloads
 through their host calls).
 
@@ -207,6 +208,57 @@ def batch_and_greeks(amc, device, reps=2, n_check=8):
     return out
 
 
+def oos_setup(amc, ctx, torch, stream, opt, value_seed):
+    """Fit the boundary on the points of opt.seed, then write the paths of
+    value_seed into S (mixed precision); returns (S, coef, res, vopt)."""
+    ld = amc.amc_path_ld(opt.n_paths)
+    S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
+    coef = torch.zeros((opt.n_steps, amc.AMC_COEF_STRIDE), dtype=torch.float64, device="cuda")
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    vopt = workloads.Option(**{**opt.as_dict(), "seed": value_seed})
+    with torch.cuda.stream(stream):
+        amc.amc_generate_paths(ctx, opt, amc.AMC_MIXED, S, stream=stream)
+        amc.amc_fit_boundary(ctx, opt, amc.AMC_MIXED, S, coef, res, stream=stream)
+        amc.amc_generate_paths(ctx, vopt, amc.AMC_MIXED, S, stream=stream)
+    stream.synchronize()
+    return S, coef, res, vopt
+
+
+def oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warmup=3):
+    """Second pass on the bench workload: the boundary valuation kernel timed
+    with CUDA events on its stream (device-resident paths, 1.06 GB > L2, so
+    every launch streams them from HBM), and the whole out-of-sample pricing
+    (two path generations, fit, valuation) through amc_price_oos."""
+    S, coef, res, vopt = oos_setup(amc, ctx, torch, stream, opt, opt.seed + 5)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            amc.amc_value_boundary(ctx, vopt, amc.AMC_MIXED, S, coef, res, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            amc.amc_value_boundary(ctx, vopt, amc.AMC_MIXED, S, coef, res, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    units = opt.n_paths * opt.n_steps
+    nbytes = 4.0 * units
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    val = amc.res_to_dict(res.cpu().numpy())
+    amc.amc_price_oos(ctx, opt, opt.seed + 5, amc.AMC_MIXED)
+    t = time.perf_counter()
+    fit, val2 = amc.amc_price_oos(ctx, opt, opt.seed + 5, amc.AMC_MIXED)
+    host_ms = (time.perf_counter() - t) * 1e3
+    return {"kernel": "value_boundary_kernel", "ms": ms, "value": units / (ms * 1e-3), "unit": METRIC,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": profile_traffic("paper_1205_0106_gb300/csrc/value.cu",
+                                                    "profiles/value_boundary_2p20x252_mixed.md"),
+                         "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
+            "price_out_of_sample": val2["price"], "std_err": val2["std_err"], "price_in_sample": fit["price"],
+            "oos_pricing_ms": host_ms,
+            "workload": "boundary fitted on shift seed 2, applied to the 2^20 x 252 paths of shift seed 7"}
+
+
 def serve_replay(amc, ctx, times, opts, slots=3, max_batch=128, prec=1):
     """Replay arrivals (seconds from start) through the serving loop.
     Returns latency percentiles, throughput and counts."""
@@ -332,6 +384,19 @@ def run_amc(args):
             return total, sum(gen) / steps, sum(swp) / steps, res
         return ev[0].elapsed_time(ev[1]), None, None, res
 
+    if args.profile_value:
+        # profiling mode: fit once, then only the valuation launches (for ncu)
+        S, coef, res, vopt = oos_setup(amc, ctx, torch, stream, opt, opt.seed + 5)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup + args.steps):
+                amc.amc_value_boundary(ctx, vopt, amc.AMC_MIXED, S, coef, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "value", "steps": args.steps, "warmup": args.warmup}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile:
         # profiling mode: only the timed mixed-precision steps (for ncu)
         t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
@@ -409,6 +474,8 @@ def run_amc(args):
             "gpu_launches": 3 * args.steps,
             "roofline": dominant, "roofline_sweep": rl_sweep, "roofline_pathgen": rl_gen,
             "clocks": ck}
+    if not args.no_oos:
+        line["oos"] = oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
     if args.serve_seconds > 0:
         times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
         sctx = amc.Context(local, arena_bytes=24 << 30)
@@ -438,11 +505,14 @@ def main():
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch and Greeks workloads")
+    ap.add_argument("--no-oos", action="store_true", help="skip the out-of-sample second pass")
+    ap.add_argument("--profile-value", action="store_true",
+                    help="run only the boundary valuation launches (for ncu captures)")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
-    if args.warmup < 3 and not args.profile:
+    if args.warmup < 3 and not (args.profile or args.profile_value):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

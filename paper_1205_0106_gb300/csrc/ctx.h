@@ -61,6 +61,8 @@ struct amc_ctx {
     double *fin1 = nullptr;
     double *res1 = nullptr;
     int32_t *status1 = nullptr;
+    double *finv = nullptr;                          // per-CTA sums of the boundary valuation (grown on demand)
+    int64_t finv_ctas = 0;
     uint64_t *xch1 = nullptr;                        // exchange units of the mixed LSM sweep
     uint32_t epoch = 0;                              // launch tag of those units
     int gcap = 0;

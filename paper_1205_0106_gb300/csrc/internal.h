@@ -135,6 +135,7 @@ cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bo
 cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
 cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStream_t st);
+int64_t value_ctas(int64_t n_paths);            // CTAs of the boundary valuation (one 2048-path slice each)
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 

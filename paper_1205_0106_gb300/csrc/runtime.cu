@@ -209,13 +209,21 @@ int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     J.S = const_cast<void *>(S);
     J.ld = ld;
     J.coef = const_cast<double *>(coef);
-    const int64_t units = (o->n_paths + 8LL * kValueThreads - 1) / (8LL * kValueThreads);
-    J.n_cta = (int)std::min<int64_t>(units, c->gcap);
-    J.fin = c->fin1;
+    const int64_t ctas = value_ctas(o->n_paths);
+    if (ctas > c->finv_ctas) {                        // grown on demand (synchronises the device once)
+        cudaFree(c->finv);
+        c->finv = nullptr;
+        c->finv_ctas = 0;
+        if (cudaMalloc(&c->finv, sizeof(double) * 4 * (size_t)ctas) != cudaSuccess) return AMC_ENOMEM;
+        c->finv_ctas = ctas;
+    }
+    J.n_cta = (int)ctas;
+    J.fin = c->finv;
     J.res = res;
     J.status = c->status1;
     a.n_jobs = 1;
     a.max_m = o->n_steps;
+    a.timeout_ns = timeout_ns(c);
     AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
     AMC_TRY_CUDA(launch_value_boundary(a, J.n_cta, prec == AMC_FP64, st));
     AMC_TRY_CUDA(launch_finalize(a, st));
@@ -590,6 +598,7 @@ int amc_ctx_destroy(amc_ctx *c) {
     cudaFree(c->part1);
     cudaFree(c->arrive1);
     cudaFree(c->fin1);
+    cudaFree(c->finv);
     cudaFree(c->res1);
     cudaFree(c->status1);
     cudaFree(c->xch1);

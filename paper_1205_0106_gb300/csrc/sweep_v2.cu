@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         if ((lane & 3) == 0 && k < nmom) sm.redG[buf][warp][k] = r;
     };
 
-    if (J.coef && lc == 0 && warp == kXW0 && lane < kCoefStride)   // maturity: no exercise decision
+    if (!GREEKS && J.coef && lc == 0 && warp == kXW0 && lane < kCoefStride)   // maturity: no exercise decision
         J.coef[(size_t)(m - 1) * kCoefStride + lane] = lane == 4 ? 1.0 : 0.0;
     if (w == 0)
         for (int d = m; d >= 1 && d > m - kSlots; --d) issue(d);
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 t = df_add(t, df_shfl_xor(t, 1));
                 t = df_add(t, df_shfl_xor(t, 2));
                 const float bk = __fadd_rn(t.hi, t.lo);
-                if (J.coef && lc == 0 && warp == kXW0) {          // fitted boundary of date j (units of K)
+                if (!GREEKS && J.coef && lc == 0 && warp == kXW0) {   // fitted boundary of date j (units of K)
                     const float ck = __shfl_sync(kFull, bk, 4 * (lane & 3));
                     const int dg = sm.gdeg[b];
                     if (lane < 4) J.coef[(size_t)(j - 1) * kCoefStride + lane] = dg ? 0.0 : (double)ck;
