@@ -11,7 +11,7 @@ L2, so every step streams it from HBM.
 
 Keys beyond the base contract: fp64 (the same step in all-FP64 on the GPU),
 err_vs_oracle (|price - FP64 oracle price| on identical points, in units of
-K), roofline (dominant kernel) and roofline_sweep, cpu_baseline (the oracle
+K, from the CPU baseline leg), roofline (dominant kernel) and roofline_sweep, cpu_baseline (the oracle
 on a bounded sample, host cores), clocks, oos (the second, out-of-sample
 pass: the boundary valuation kernel and its HBM roofline), serving (a Poisson request replay),
 batch and greeks (the 4096-option batch and 1024-option Greeks workloads
@@ -153,25 +153,25 @@ def _peaks():
 
 def cpu_baseline(opt, n_sample=None):
     """The FP64 oracle as it stands on a bounded sample (first n_sample paths; default all of them,
-    about 5 s on 16 host cores). A 64-path call first loads the library and its tables."""
+    about 5 s on 16 host cores). A 64-path call first loads the library and its tables.  With the
+    whole workload as the sample, the oracle price on the bench's own points comes back too."""
     import oracle
     n_sample = opt.n_paths if n_sample is None else n_sample
     oracle.lsm(oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, 64, opt.seed),
                opt.type, opt.K, opt.r, opt.T, opt.basis)
     t = time.perf_counter()
     S = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, n_sample, opt.seed)
-    oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
+    res = oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
     dt = time.perf_counter() - t
-    return {"value": n_sample * opt.n_steps / dt, "unit": METRIC, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "first %d of %d paths, all %d dates, paths + LSM sweep, %.1f s" % (
-                n_sample, opt.n_paths, opt.n_steps, dt)}
+    out = {"value": n_sample * opt.n_steps / dt, "unit": METRIC, "cores": oracle.threads(), "kind": "oracle",
+           "sample": "first %d of %d paths, all %d dates, paths + LSM sweep, %.1f s" % (
+               n_sample, opt.n_paths, opt.n_steps, dt)}
+    return out, (res["price"] if n_sample == opt.n_paths else None)
 
 
-def batch_and_greeks(amc, device, reps=2, n_check=8):
+def batch_and_greeks(amc, device, reps=2):
     """The 4096-option batch and the 1024-option Greeks workloads through their host calls
-    (host buffers in and out, so wall time), each after one warm-up call; the batch price
-    of a seeded sample of n_check options is checked against the FP64 oracle."""
-    import numpy as np
+    (host buffers in and out, so wall time), each after one warm-up call."""
     bctx = amc.Context(device, arena_bytes=32 << 30)
     out = {}
     opts = workloads.batch_options()
@@ -184,17 +184,6 @@ def batch_and_greeks(amc, device, reps=2, n_check=8):
     failed = sum(r["status"] != 0 for r in res)
     out["batch"] = {"options": len(opts), "path_steps": steps, "s": dt, "value": steps / dt, "unit": METRIC,
                     "failed": failed, "workload": "4096 options, seed 3, 2^14..2^18 paths, 12..365 dates, p = 3"}
-    if n_check:
-        import oracle
-        idx = np.random.default_rng(7).choice(len(opts), n_check, replace=False)
-        errs = []
-        for i in idx:
-            o = opts[i]
-            ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
-                               seed=o.seed)
-            errs.append(abs(res[i]["price"] - ref["price"]) / o.K)
-        out["batch"]["oracle_sample"] = n_check
-        out["batch"]["oracle_max_err_over_K"] = max(errs)
     gopts = workloads.greeks_options()
     gsteps = sum(o.path_steps for o in gopts)
     amc.amc_greeks(bctx, gopts, amc.AMC_MIXED)
@@ -257,6 +246,54 @@ def oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warmup=3):
             "price_out_of_sample": val2["price"], "std_err": val2["std_err"], "price_in_sample": fit["price"],
             "oos_pricing_ms": host_ms,
             "workload": "boundary fitted on shift seed 2, applied to the 2^20 x 252 paths of shift seed 7"}
+
+
+def paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warmup=3):
+    """The paper's own exercise rule (Eqs. 10-11) on the bench workload's
+    paths: its sweep alone, timed with CUDA events on its stream (paths
+    resident, 1.06 GB > L2).  The rule reads the dates 1..m-1 once."""
+    popt = workloads.Option(**{**opt.as_dict(), "rule": workloads.RULE_PAPER_UB})
+    ld = amc.amc_path_ld(opt.n_paths)
+    S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        amc.amc_generate_paths(ctx, popt, amc.AMC_MIXED, S, stream=stream)
+        for _ in range(warmup):
+            amc.amc_sweep(ctx, popt, amc.AMC_MIXED, S, res, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            amc.amc_sweep(ctx, popt, amc.AMC_MIXED, S, res, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 4.0 * opt.n_paths * (opt.n_steps - 1)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    got = amc.res_to_dict(res.cpu().numpy())
+    return {"kernel": "sweep_pathwise_kernel (paper rule)", "ms": ms,
+            "value": opt.n_paths * opt.n_steps / (ms * 1e-3), "unit": METRIC,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
+            "price": got["price"], "workload": "Eqs. 10-11 on the 2^20 x 252 paths of shift seed 2"}
+
+
+def fig1_bench(amc, device):
+    """The paper's Fig. 1 data: value vs number of exercise dates for LSM and
+    the paper's rule (the Longstaff-Schwartz Table 1 put, 2^16 paths), all
+    points in one batch call, mixed precision."""
+    bctx = amc.Context(device, arena_bytes=4 << 30)
+    opts = workloads.fig1_options()
+    amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+    t = time.perf_counter()
+    res = amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+    dt = time.perf_counter() - t
+    bctx.close()
+    n = len(workloads.FIG1_DATES)
+    return {"dates": list(workloads.FIG1_DATES),
+            "lsm": [round(r["price"], 5) for r in res[:n]], "lsm_std_err": [round(r["std_err"], 5) for r in res[:n]],
+            "paper_rule": [round(r["price"], 5) for r in res[n:]], "s": dt,
+            "workload": "put S0 36 K 40 r 0.06 sigma 0.2 T 1, basis 3, 2^16 paths, shift seed 21"}
 
 
 def serve_replay(amc, ctx, times, opts, slots=3, max_batch=128, prec=1):
@@ -456,18 +493,12 @@ def run_amc(args):
               "kernel": "pathgen_kernel", "ms": gen_ms, "peak_kind": peak_kind, "algorithmic_bytes": bytes_gen,
               "note": "issue-bound (ALU); the HBM write fraction is the secondary bound"}
     dominant = rl_gen if gen_ms >= sweep_ms else rl_sweep
-    err = None
-    if not args.no_oracle_check:
-        import oracle
-        ref = oracle.price(opt.S0, opt.K, opt.r, opt.sigma, opt.T, opt.n_steps, opt.n_paths, basis=opt.basis,
-                           type=opt.type, seed=opt.seed)
-        err = abs(price["price"] - ref["price"]) / opt.K
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": _config(opt, {"parallelism": "replicas" if ws > 1 else "single"}),
             "price": price["price"], "std_err": price["std_err"],
-            "err_vs_oracle_over_K": err,
+            "err_vs_oracle_over_K": None,
             "fp64": {"value": units * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "price": fp64_price,
                      "mixed_over_fp64": fp64_ms / ms_per_step},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 64},
@@ -476,6 +507,7 @@ def run_amc(args):
             "clocks": ck}
     if not args.no_oos:
         line["oos"] = oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
+        line["paper_rule"] = paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
     if args.serve_seconds > 0:
         times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
         sctx = amc.Context(local, arena_bytes=24 << 30)
@@ -487,8 +519,12 @@ def run_amc(args):
         sctx.close()
     if not args.no_batch:
         line.update(batch_and_greeks(amc, local))
+        line["fig1"] = fig1_bench(amc, local)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(opt)
+        # the oracle on the whole workload: the CPU baseline, and its price on the same points
+        line["cpu_baseline"], ref_price = cpu_baseline(opt)
+        if ref_price is not None:
+            line["err_vs_oracle_over_K"] = abs(price["price"] - ref_price) / opt.K
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
@@ -502,7 +538,6 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["amc", "reference"], default="amc")
-    ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch and Greeks workloads")
     ap.add_argument("--no-oos", action="store_true", help="skip the out-of-sample second pass")

@@ -381,3 +381,25 @@ def test_out_of_sample_price_is_low_biased_against_the_bermudan_tree():
     assert val["price"] <= tree + 3.0 * val["std_err"]
     assert val["price"] >= tree - 0.01 * tree
     assert val["price"] > oracle.bs(oracle.PUT, 36.0, 40.0, .06, .2, 1.0)
+
+
+# ------------------------------------------- value vs number of exercise dates
+def test_fig1_shape_in_the_oracle():
+    """One date is the European estimator; the LSM value grows with nested
+    date grids (within the RQMC error) toward the American tree value; the
+    paper's pathwise rule stays above LSM."""
+    import workloads
+    dates = (1, 2, 4, 8, 16, 32, 64)
+    lsm = {o.n_steps: oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, 2 ** 13, basis=o.basis, seed=o.seed)
+           for o in workloads.fig1_options(dates, rules=(oracle.RULE_LSM,))}
+    ub = {o.n_steps: oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, 2 ** 13, seed=o.seed, rule=o.rule)
+          for o in workloads.fig1_options(dates, rules=(oracle.RULE_PAPER_UB,))}
+    S1 = oracle.paths(36.0, .06, .2, 1.0, 1, 2 ** 13, 21)
+    assert lsm[1]["price"] == pytest.approx(oracle.european(S1, oracle.PUT, 40.0, .06, 1.0)["price"], rel=1e-14)
+    for a, b in zip(dates, dates[1:]):
+        assert lsm[b]["price"] >= lsm[a]["price"] - 3 * (lsm[a]["std_err"] + lsm[b]["std_err"])
+    american = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000)
+    assert american - 0.03 * american <= lsm[64]["price"] <= american + 3 * lsm[64]["std_err"]
+    assert lsm[64]["price"] - lsm[1]["price"] > 0.5          # early exercise is worth ~0.6 here
+    for m in dates:
+        assert ub[m]["price"] >= lsm[m]["price"] - 3 * lsm[m]["std_err"]

@@ -102,3 +102,15 @@ def scaled(opt, n_paths=None, n_steps=None):
     if n_steps is not None:
         d["n_steps"] = n_steps
     return Option(**d)
+
+
+FIG1_DATES = (1, 2, 4, 8, 16, 32, 64, 128, 256)
+
+
+def fig1_options(dates=FIG1_DATES, n_paths=2 ** 16, seed=21, rules=(RULE_LSM, RULE_PAPER_UB)):
+    """Value vs number of exercise dates (the paper's Fig. 1, which prints no
+    parameters): the Longstaff-Schwartz Table 1 put (S0 36, K 40, r 6 %,
+    sigma 20 %, T 1 year, basis 3) on the same shift seed for every m; the
+    power-of-two date grids are nested.  Ordered rule-major, then by m."""
+    return [Option(36.0, 40.0, 0.06, 0.2, 1.0, m, n_paths, basis=3, type=PUT, seed=seed, rule=rule)
+            for rule in rules for m in dates]
