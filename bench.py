@@ -274,7 +274,9 @@ def paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warm
     return {"kernel": "sweep_pathwise_kernel (paper rule)", "ms": ms,
             "value": opt.n_paths * opt.n_steps / (ms * 1e-3), "unit": METRIC,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
+                         "traffic": profile_traffic("paper_1205_0106_gb300/csrc/sweep.cu",
+                                                    "profiles/sweep_pathwise_paper_2p20x252_mixed.md"),
+                         "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
             "price": got["price"], "workload": "Eqs. 10-11 on the 2^20 x 252 paths of shift seed 2"}
 
 
@@ -421,6 +423,22 @@ def run_amc(args):
             return total, sum(gen) / steps, sum(swp) / steps, res
         return ev[0].elapsed_time(ev[1]), None, None, res
 
+    if args.profile_paper:
+        # profiling mode: the paper-rule sweep on resident paths (for ncu)
+        popt = workloads.Option(**{**opt.as_dict(), "rule": workloads.RULE_PAPER_UB})
+        S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            amc.amc_generate_paths(ctx, popt, amc.AMC_MIXED, S, stream=stream)
+            for _ in range(args.warmup + args.steps):
+                amc.amc_sweep(ctx, popt, amc.AMC_MIXED, S, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "paper", "steps": args.steps, "warmup": args.warmup}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile_value:
         # profiling mode: fit once, then only the valuation launches (for ncu)
         S, coef, res, vopt = oos_setup(amc, ctx, torch, stream, opt, opt.seed + 5)
@@ -543,11 +561,13 @@ def main():
     ap.add_argument("--no-oos", action="store_true", help="skip the out-of-sample second pass")
     ap.add_argument("--profile-value", action="store_true",
                     help="run only the boundary valuation launches (for ncu captures)")
+    ap.add_argument("--profile-paper", action="store_true",
+                    help="run only the paper-rule sweeps (for ncu captures)")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
-    if args.warmup < 3 and not (args.profile or args.profile_value):
+    if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
