@@ -37,6 +37,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
@@ -60,6 +61,14 @@ def _lib():
         lib.orc_bridge_schedule.argtypes = [ctypes.c_int, _ip, _ip, _ip]
         lib.orc_paths.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _u32p, _u32p,
                                                           _dp, _dp]
+        lib.orc_lcg_modulus.argtypes = [ctypes.c_int64]
+        lib.orc_lcg_modulus.restype = ctypes.c_uint64
+        lib.orc_lcg_params.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, _u64p, _u64p]
+        lib.orc_lcg_perm.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                     ctypes.c_uint64]
+        lib.orc_lcg_perm.restype = ctypes.c_uint64
+        lib.orc_paths_permuted.argtypes = ([ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, _u32p, _u64p, _u64p,
+                                                                    _dp])
         lib.orc_bs.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5
         lib.orc_bs.restype = ctypes.c_double
         lib.orc_solve_normal.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -169,6 +178,34 @@ def paths(S0, r, sigma, T, m, N, seed, with_W=False, first=0):
     if rc != 0:
         raise MemoryError("oracle path generation failed (%d)" % rc)
     return (S, W) if with_W else S
+
+
+def lcg_params(seed, m, N):
+    """Per-dimension (a_d, c_d) and the modulus M of the paper's LCG permutation."""
+    a = np.zeros(m, dtype=np.uint64)
+    c = np.zeros(m, dtype=np.uint64)
+    _lib().orc_lcg_params(seed, m, N, _ptr(a, _u64p), _ptr(c, _u64p))
+    return a, c, int(_lib().orc_lcg_modulus(N))
+
+
+def lcg_perm(seed, d, N, i):
+    """pi_d(i) for the points 0..N-1 (vectorised over i with a Python loop)."""
+    a, c, M = lcg_params(seed, d + 1, N)
+    f = _lib().orc_lcg_perm
+    return np.array([f(int(a[d]), int(c[d]), M, N, int(k)) for k in np.atleast_1d(i)], dtype=np.int64)
+
+
+def paths_permuted(S0, r, sigma, T, m, N, seed):
+    """Steps 1-3 with the paper's LCG permutation of each dimension's
+    (unshifted) quasi-random array instead of the digital shift."""
+    V = directions(m)
+    a, c, _ = lcg_params(seed, m, N)
+    S = np.empty((m, N), dtype=np.float64)
+    rc = _lib().orc_paths_permuted(S0, r, sigma, T, m, N, _ptr(V, _u32p), _ptr(a, _u64p), _ptr(c, _u64p),
+                                   _ptr(S, _dp))
+    if rc != 0:
+        raise MemoryError("oracle permuted path generation failed (%d)" % rc)
+    return S
 
 
 def bs(type_, S, K, r, sigma, T):

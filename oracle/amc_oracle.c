@@ -292,6 +292,79 @@ int orc_paths(double S0, double r, double sigma, double T, int m, int64_t N, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's randomisation (§III.D): each quasi-random array (dimension)
+ * is permuted by a linear congruential generator.  Reading: path i takes
+ * the unshifted Sobol' point pi_d(i) in dimension d, where
+ *   pi_d(i) = L_d(i), repeated (L_d applied again) while the value is >= N,
+ *   L_d(x) = (a_d x + c_d) mod M,  M = least power of two >= N,
+ * with a_d = 1 mod 4 and c_d odd, so L_d has full period M (Hull-Dobell)
+ * and walking its cycle back into 0..N-1 makes pi_d a permutation of them.
+ * a_d = 4 (r_{2d} mod max(M/4, 1)) + 1 and c_d = (r_{2d+1} mod M) | 1 (mod M), with r_k
+ * the k-th output of SplitMix64(seed).                                      */
+uint64_t orc_lcg_modulus(int64_t N)
+{
+    uint64_t M = 1;
+    while ((int64_t)M < N) M <<= 1;
+    return M;
+}
+
+void orc_lcg_params(uint64_t seed, int m, int64_t N, uint64_t *a, uint64_t *c)
+{
+    uint64_t state = seed, M = orc_lcg_modulus(N);
+    uint64_t q = M >= 4 ? M / 4 : 1;
+    for (int d = 0; d < m; ++d) {
+        uint64_t r0 = orc_splitmix64_next(&state), r1 = orc_splitmix64_next(&state);
+        a[d] = (4 * (r0 % q) + 1) % M;
+        c[d] = ((r1 % M) | 1) % M;
+        if (M == 1) a[d] = c[d] = 0;
+    }
+}
+
+uint64_t orc_lcg_perm(uint64_t a, uint64_t c, uint64_t M, int64_t N, uint64_t i)
+{
+    uint64_t x = (a * i + c) & (M - 1);
+    while ((int64_t)x >= N) x = (a * x + c) & (M - 1);
+    return x;
+}
+
+/* Paths as orc_paths, with the permuted unshifted points in place of the
+ * digitally shifted ones (points 0..N-1 only).                             */
+int orc_paths_permuted(double S0, double r, double sigma, double T, int m, int64_t N, const uint32_t *V,
+                       const uint64_t *a, const uint64_t *c, double *S)
+{
+    int *date = (int *)malloc(sizeof(int) * (size_t)m);
+    int *left = (int *)malloc(sizeof(int) * (size_t)m);
+    int *right = (int *)malloc(sizeof(int) * (size_t)m);
+    int bad = 0;
+    if (!date || !left || !right || orc_bridge_schedule(m, date, left, right) != 0) {
+        free(date); free(left); free(right);
+        return -1;
+    }
+    const uint64_t M = orc_lcg_modulus(N);
+    double dt = T / m;
+    double mu = r - 0.5 * sigma * sigma;
+#pragma omp parallel reduction(| : bad)
+    {
+        double *z = (double *)malloc(sizeof(double) * (size_t)m);
+        double *W = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+        if (!z || !W) bad |= 1;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            if (!z || !W) continue;
+            for (int k = 0; k < m; ++k) {
+                uint64_t j = orc_lcg_perm(a[k], c[k], M, N, (uint64_t)i);
+                z[k] = orc_norm_icdf(orc_uniform(orc_sobol_direct(V, k, j)));
+            }
+            orc_bridge_apply(m, dt, date, left, right, z, W);
+            for (int j = 1; j <= m; ++j) S[(int64_t)(j - 1) * N + i] = S0 * exp(mu * (j * dt) + sigma * W[j]);
+        }
+        free(z); free(W);
+    }
+    free(date); free(left); free(right);
+    return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 static double orc_payoff(int type, double S, double K)
 {
     double h = type == ORC_CALL ? S - K : K - S;

@@ -403,3 +403,52 @@ def test_fig1_shape_in_the_oracle():
     assert lsm[64]["price"] - lsm[1]["price"] > 0.5          # early exercise is worth ~0.6 here
     for m in dates:
         assert ub[m]["price"] >= lsm[m]["price"] - 3 * lsm[m]["std_err"]
+
+
+# ------------------------------------------ the paper's LCG-permuted points
+@pytest.mark.parametrize("N", [1, 2, 3, 1000, 4096, 12345])
+def test_lcg_permutation_is_a_bijection(N):
+    for d in (0, 5):
+        p = oracle.lcg_perm(11, d, N, np.arange(N))
+        assert np.array_equal(np.sort(p), np.arange(N))
+
+
+def test_lcg_map_has_full_period():
+    """Hull-Dobell: a = 1 mod 4, c odd => x -> a x + c (mod 2^k) is one cycle."""
+    a, c, M = oracle.lcg_params(3, 4, 1000)
+    assert M == 1024
+    for d in range(4):
+        assert a[d] % 4 == 1 and c[d] % 2 == 1
+        x, seen = 0, set()
+        for _ in range(M):
+            seen.add(x)
+            x = (int(a[d]) * x + int(c[d])) % M
+        assert x == 0 and len(seen) == M
+
+
+def test_permuted_paths_rebuilt_from_scipy_points():
+    """Path i = GBM of the bridge of ndtri(u) of the unshifted Sobol' points
+    pi_d(i) (scipy's points, the pinned bridge matrix)."""
+    from scipy.stats import qmc
+    from scipy.special import ndtri
+    m, N, seed, S0, r, sig, T = 16, 700, 9, 36.0, .06, .2, 1.0
+    S = oracle.paths_permuted(S0, r, sig, T, m, N, seed)
+    pts = qmc.Sobol(d=m, scramble=False, bits=32).random(1024)
+    X = np.round(pts * 2.0 ** 32).astype(np.uint64)            # integer points 0..1023
+    A = oracle.bridge_matrix(m, T)
+    t = np.arange(1, m + 1) * (T / m)
+    for i in (0, 1, 2, 345, 699):
+        j = [int(oracle.lcg_perm(seed, d, N, i)[0]) for d in range(m)]
+        u = (X[j, np.arange(m)].astype(np.float64) + 0.5) / 2.0 ** 32
+        W = A @ ndtri(u)
+        want = S0 * np.exp((r - 0.5 * sig * sig) * t + sig * W)
+        np.testing.assert_allclose(S[:, i], want, rtol=1e-12)
+
+
+def test_permuted_points_give_an_unbiased_lsm_price():
+    p_perm = [oracle.lsm(oracle.paths_permuted(36., .06, .2, 1., 16, 2 ** 12, s), oracle.PUT, 40., .06, 1., 3)
+              for s in range(6)]
+    mean = np.mean([q["price"] for q in p_perm])
+    se = np.std([q["price"] for q in p_perm], ddof=1) / np.sqrt(len(p_perm))
+    ref = oracle.price(36., 40., .06, .2, 1., 16, 2 ** 16, basis=3, seed=1)
+    assert abs(mean - ref["price"]) < 4 * se + 3 * ref["std_err"] + 0.01
