@@ -298,6 +298,44 @@ def fig1_bench(amc, device):
             "workload": "put S0 36 K 40 r 0.06 sigma 0.2 T 1, basis 3, 2^16 paths, shift seed 21"}
 
 
+def randomization_bench(amc, ctx, torch, stream, opt, R=32):
+    """The paper's randomisation (LCG permutation of each dimension's points)
+    vs the digital shift: the spread of the LSM price over R independent
+    seeds (LS Table 1 put, 50 dates, 2^16 paths, mixed), and the permuted
+    path generation timed on the bench workload."""
+    base = workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 50, 2 ** 16, basis=3, seed=0)
+    seeds = [1000 + s for s in range(R)]
+    shifted = [r["price"] for r in amc.amc_price_batch(ctx, [workloads.Option(**{**base.as_dict(), "seed": s})
+                                                             for s in seeds], amc.AMC_MIXED)]
+    ld = amc.amc_path_ld(base.n_paths)
+    S = torch.empty((base.n_steps, ld), dtype=torch.float32, device="cuda")
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    permuted = []
+    with torch.cuda.stream(stream):
+        for s in seeds:
+            o = workloads.Option(**{**base.as_dict(), "seed": s})
+            amc.amc_generate_paths_permuted(ctx, o, amc.AMC_MIXED, S, stream=stream)
+            amc.amc_sweep(ctx, o, amc.AMC_MIXED, S, res, stream=stream)
+            stream.synchronize()
+            permuted.append(float(res[0].item()))
+        # permuted path generation on the bench workload
+        Sb = torch.empty((opt.n_steps, amc.amc_path_ld(opt.n_paths)), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            amc.amc_generate_paths_permuted(ctx, opt, amc.AMC_MIXED, Sb, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            amc.amc_generate_paths_permuted(ctx, opt, amc.AMC_MIXED, Sb, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    sd_s, sd_p = statistics.stdev(shifted), statistics.stdev(permuted)
+    return {"seeds": R, "digital_shift_mean": statistics.fmean(shifted), "digital_shift_sd": sd_s,
+            "lcg_permutation_mean": statistics.fmean(permuted), "lcg_permutation_sd": sd_p,
+            "variance_ratio_perm_over_shift": (sd_p / sd_s) ** 2 if sd_s > 0 else None,
+            "permuted_pathgen_ms_bench_workload": e0.elapsed_time(e1) / 5,
+            "workload": "LSM price over %d seeds: put S0 36 K 40 r 0.06 sigma 0.2 T 1, 50 dates, 2^16 paths" % R}
+
+
 def serve_replay(amc, ctx, times, opts, slots=3, max_batch=128, prec=1):
     """Replay arrivals (seconds from start) through the serving loop.
     Returns latency percentiles, throughput and counts."""
@@ -526,6 +564,7 @@ def run_amc(args):
     if not args.no_oos:
         line["oos"] = oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
         line["paper_rule"] = paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
+        line["randomization"] = randomization_bench(amc, ctx, torch, stream, opt)
     if args.serve_seconds > 0:
         times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
         sctx = amc.Context(local, arena_bytes=24 << 30)

@@ -150,6 +150,21 @@ int amc_sobol(amc_ctx *ctx, int n_dims, int64_t n_points, uint64_t seed,
  * points; nothing beyond ld is written.                                    */
 int amc_generate_paths(amc_ctx *ctx, const amc_option *opt, int prec,
                        void *S_dev, int64_t ld, void *stream);
+/* Steps 1-3 with the paper's randomisation of the points (§III.D) in place
+ * of the digital shift: each dimension's array of quasi-random points is
+ * permuted by a linear congruential generator.  Path i takes the unshifted
+ * Sobol' point pi_d(i) in dimension d, pi_d(i) = L_d(i) applied again while
+ * the value is >= n_paths, L_d(x) = (a_d x + c_d) mod M; M is the least
+ * power of two >= n_paths, a_d = 1 mod 4 and c_d odd (full period, so pi_d
+ * is a permutation of 0..n_paths-1); a_d and c_d come from outputs 2d and
+ * 2d+1 of SplitMix64(opt->seed) (amc_lcg_params).  Storage, layout and
+ * errors as amc_generate_paths; the sweeps take these paths unchanged.    */
+int amc_generate_paths_permuted(amc_ctx *ctx, const amc_option *opt, int prec,
+                                void *S_dev, int64_t ld, void *stream);
+/* The permutation's parameters of dimensions 0..n_dims-1 for n_points
+ * points: a[d] = 4 (r_2d mod max(M/4, 1)) + 1, c[d] = (r_2d+1 mod M) | 1,
+ * *M the modulus.  No GPU.                                                 */
+int amc_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uint32_t *c, uint64_t *M);
 /* Step 4 on caller paths S (as written by amc_generate_paths), result into
  * res_dev[AMC_RES_DOUBLES].  with_greeks != 0 also fills delta and vega
  * (frozen exercise boundary).  Asynchronous.                               */

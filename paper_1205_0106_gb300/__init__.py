@@ -85,6 +85,8 @@ SIGNATURES = {
     "amc_generate_paths": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp]),
     "amc_sweep": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "amc_price_device": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "amc_generate_paths_permuted": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp]),
+    "amc_lcg_params": (ctypes.c_int, [_u64, ctypes.c_int, _i64, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
     "amc_fit_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_value_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_price_oos": (ctypes.c_int, [_vp, _optp, _u64, ctypes.c_int, _resp, _resp]),
@@ -274,6 +276,24 @@ def amc_price_device(ctx, opt, prec, S, res, ld=None, stream=None):
     ld = S.shape[1] if ld is None else ld
     _check(lib().amc_price_device(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(res),
                                   _stream(stream)), "amc_price_device")
+
+
+def amc_generate_paths_permuted(ctx, opt, prec, S, ld=None, stream=None):
+    """Paths from the paper's LCG-permuted (unshifted) quasi-random points."""
+    ld = S.shape[1] if ld is None else ld
+    _check(lib().amc_generate_paths_permuted(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld,
+                                             _stream(stream)), "amc_generate_paths_permuted")
+
+
+def amc_lcg_params(seed, n_dims, n_points):
+    """(a[n_dims], c[n_dims], M) of the LCG permutation (host only)."""
+    import numpy as np
+    a = np.zeros(n_dims, dtype=np.uint32)
+    c = np.zeros(n_dims, dtype=np.uint32)
+    M = ctypes.c_uint64(0)
+    _check(lib().amc_lcg_params(seed, n_dims, n_points, a.ctypes.data_as(_vp), c.ctypes.data_as(_vp),
+                                ctypes.byref(M)), "amc_lcg_params")
+    return a, c, M.value
 
 
 def amc_fit_boundary(ctx, opt, prec, S, coef, res, ld=None, stream=None):

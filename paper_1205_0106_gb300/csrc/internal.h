@@ -40,6 +40,7 @@ struct BridgePlan {
 // Host tables (tables.cpp).
 int host_directions(int n_dims, uint32_t *V);
 void host_shifts(uint64_t seed, int n_dims, uint32_t *out);
+void host_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uint32_t *c, uint64_t *M);
 int host_bridge_bfs(int m, int32_t *date, int32_t *left, int32_t *right);
 int host_bridge_plan(int m, BridgePlan *plan);
 int host_validate(const amc_option *o);
@@ -135,6 +136,17 @@ cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bo
 cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
 cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStream_t st);
+
+// Path generation from the LCG-permuted unshifted points (one option).
+struct PermArgs {
+    Job one;
+    const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
+    int64_t total;                  // tiles of kTilePoints points
+    int32_t max_slots;
+    uint32_t log2M;                 // modulus M = 2^log2M >= N
+    uint32_t a[AMC_MAX_STEPS], c[AMC_MAX_STEPS];
+};
+cudaError_t launch_pathgen_permuted(const PermArgs &a, bool fp64, int sm_count, cudaStream_t st);
 int64_t value_ctas(int64_t n_paths);            // CTAs of the boundary valuation (one 2048-path slice each)
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);

@@ -157,6 +157,63 @@ struct alignas(4 * sizeof(Real)) R4 {
     Real v[4];
 };
 
+// The 4 points of one bridge node: z = N^{-1}(u) of the Sobol' integers xq,
+// W = wl W_left + wr W_right + sd z (ref. [13]), S = S0 exp(drift + sig W)
+// (Eq. 9 in log space; base 2 in FP32).
+template <bool FP64, typename Real>
+__device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Real wr, Real sd, Real drift,
+                                            Real sig, Real S0, const R4<Real> &Wl, const R4<Real> &Wr,
+                                            R4<Real> &Wo, R4<Real> &So) {
+    if (FP64) {
+        Real z[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[q] = (Real)normcdfinv(((double)xq[q] + 0.5) * 0x1p-32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
+            Wo.v[q] = W;
+            So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
+        }
+    } else {
+        // points (0, 1) and (2, 3) as packed pairs: central-region
+        // values straight-line, then the rare tails, then bridge and GBM
+        using namespace dev;
+        float z[4], yv[4];
+        bool tail = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const f2 y = f2_fma(f2_pack((float)(int32_t)(xq[2 * h] ^ 0x80000000u),
+                                        (float)(int32_t)(xq[2 * h + 1] ^ 0x80000000u)),
+                                f2_splat(0x1p-32f), f2_splat(0x1p-33f));
+            const f2 zc = icdf_central2(y);
+            yv[2 * h] = f2_lo(y);
+            yv[2 * h + 1] = f2_hi(y);
+            z[2 * h] = f2_lo(zc);
+            z[2 * h + 1] = f2_hi(zc);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < 0.4983f);
+        if (tail) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q], yv[q]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const f2 W = f2_fma(f2_splat((float)sd), f2_pack(z[2 * h], z[2 * h + 1]),
+                                f2_fma(f2_splat((float)wr), f2_pack((float)Wr.v[2 * h], (float)Wr.v[2 * h + 1]),
+                                       f2_mul(f2_splat((float)wl),
+                                              f2_pack((float)Wl.v[2 * h], (float)Wl.v[2 * h + 1]))));
+            const f2 e = f2_fma(f2_splat((float)sig), W, f2_splat((float)drift));
+            const f2 Sv = f2_mul(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))));
+            Wo.v[2 * h] = (Real)f2_lo(W);
+            Wo.v[2 * h + 1] = (Real)f2_hi(W);
+            So.v[2 * h] = (Real)f2_lo(Sv);
+            So.v[2 * h + 1] = (Real)f2_hi(Sv);
+        }
+    }
+}
+
 template <bool FP64>
 __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_constant__ KArgs a) {
     using Real = typename PG<FP64>::Real;
@@ -230,58 +287,92 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
             const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
             R4<Real> Wo, So;
-            if (FP64) {
-                Real z[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) z[q] = (Real)normcdfinv(((double)xq[q] + 0.5) * 0x1p-32);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
-                    Wo.v[q] = W;
-                    So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
-                }
-            } else {
-                // points (0, 1) and (2, 3) as packed pairs: central-region
-                // values straight-line, then the rare tails, then bridge and GBM
-                using namespace dev;
-                float z[4], yv[4];
-                bool tail = false;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const f2 y = f2_fma(f2_pack((float)(int32_t)(xq[2 * h] ^ 0x80000000u),
-                                                (float)(int32_t)(xq[2 * h + 1] ^ 0x80000000u)),
-                                        f2_splat(0x1p-32f), f2_splat(0x1p-33f));
-                    const f2 zc = icdf_central2(y);
-                    yv[2 * h] = f2_lo(y);
-                    yv[2 * h + 1] = f2_hi(y);
-                    z[2 * h] = f2_lo(zc);
-                    z[2 * h + 1] = f2_hi(zc);
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < 0.4983f);
-                if (tail) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q], yv[q]);
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const f2 W = f2_fma(f2_splat((float)sd), f2_pack(z[2 * h], z[2 * h + 1]),
-                                        f2_fma(f2_splat((float)wr), f2_pack((float)Wr.v[2 * h], (float)Wr.v[2 * h + 1]),
-                                               f2_mul(f2_splat((float)wl),
-                                                      f2_pack((float)Wl.v[2 * h], (float)Wl.v[2 * h + 1]))));
-                    const f2 e = f2_fma(f2_splat((float)sig), W, f2_splat((float)drift));
-                    const f2 Sv = f2_mul(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))));
-                    Wo.v[2 * h] = (Real)f2_lo(W);
-                    Wo.v[2 * h + 1] = (Real)f2_hi(W);
-                    So.v[2 * h] = (Real)f2_lo(Sv);
-                    So.v[2 * h + 1] = (Real)f2_hi(Sv);
-                }
-            }
+            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
             s_W[nd.so * kPathgenThreads + tid] = Wo;
             if (store) {
                 Real *dst = S + (int64_t)(nd.date - 1) * ld;
                 if (FP64) {                                               // two 16-byte stores
+                    reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
+                    reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
+                } else {
+                    *reinterpret_cast<float4 *>(dst) = make_float4((float)So.v[0], (float)So.v[1],
+                                                                   (float)So.v[2], (float)So.v[3]);
+                }
+            }
+        }
+    }
+}
+
+// Path generation from the paper's randomised points (§III.D, read as a
+// permutation of each dimension's quasi-random array by a linear
+// congruential generator): path i takes the unshifted Sobol' point pi_d(i)
+// in dimension d, pi_d(i) = L_d(i) walked back into 0..N-1, L_d(x) =
+// (a_d x + c_d) mod 2^log2M with a_d = 1 mod 4 and c_d odd (full period, so
+// pi_d is a permutation).  Neighbouring paths no longer share Gray-code
+// structure, so every point is formed on its own from the direction
+// numbers; the bridge, GBM and stores are those of pathgen_kernel.
+template <bool FP64>
+__global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __grid_constant__ PermArgs a) {
+    using Real = typename PG<FP64>::Real;
+    using Node = typename PG<FP64>::Node;
+    extern __shared__ __align__(32) unsigned char smem[];
+    const Job &J = a.one;
+    const int m = J.m, nslots = J.nslots;
+    const PathgenSmem L = pathgen_layout(m, a.max_slots, FP64);
+    Node *s_nodes = reinterpret_cast<Node *>(smem + L.nodes);
+    R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);
+    const uint32_t *__restrict__ V = a.V;
+    const int tid = threadIdx.x;
+    const uint64_t mask = (1ull << a.log2M) - 1ull;
+    const uint64_t N = (uint64_t)J.N;
+    const Node *gn = reinterpret_cast<const Node *>(J.nodes);
+    for (int i = tid; i < m; i += kPathgenThreads) s_nodes[i] = gn[i];
+    const int64_t ld = J.ld;
+    const double mu = J.r - 0.5 * J.sigma * J.sigma;
+    const Real sqdt = (Real)sqrt(J.dt);
+    const Real S0 = (Real)J.S0;
+    const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
+    const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
+    for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile * kTilePoints;
+        __syncthreads();                                                  // previous tile done with smem
+        {
+            R4<Real> zero;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
+            s_W[(nslots - 1) * kPathgenThreads + tid] = zero;
+        }
+        __syncthreads();
+        const bool store = (int64_t)(base + 4u * tid) < ld;
+        Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + 4u * tid;
+        for (int n = 0; n < m; ++n) {
+            const Node nd = s_nodes[n];
+            const uint32_t ad = a.a[nd.coord], cd = a.c[nd.coord];
+            const uint32_t *__restrict__ Vd = V + nd.coord * 32;
+            uint32_t xq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint64_t i = base + 4u * tid + q;
+                uint64_t j = 0;
+                if (i < N) {
+                    j = ((uint64_t)ad * i + cd) & mask;
+                    while (j >= N) j = ((uint64_t)ad * j + cd) & mask;
+                }
+                const uint32_t g = (uint32_t)(j ^ (j >> 1));
+                uint32_t x = 0;
+                for (uint32_t b = 0; b < a.log2M; ++b) x ^= __ldg(Vd + b) & (0u - ((g >> b) & 1u));
+                xq[q] = x;
+            }
+            const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
+            const Real drift = mu_dt * (Real)nd.date;
+            const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
+            const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
+            R4<Real> Wo, So;
+            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
+            s_W[nd.so * kPathgenThreads + tid] = Wo;
+            if (store) {
+                Real *dst = S + (int64_t)(nd.date - 1) * ld;
+                if (FP64) {
                     reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
                     reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
                 } else {
@@ -310,6 +401,22 @@ cudaError_t launch_sobol(const uint32_t *V, int n_dims, int64_t n_points, const 
     if (n_points <= 0) return cudaSuccess;
     dim3 grid((unsigned)((n_points + 255) / 256), (unsigned)n_dims);
     sobol_kernel<<<grid, 256, 0, st>>>(V, n_dims, n_points, shift, x, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pathgen_permuted(const PermArgs &a, bool fp64, int sm_count, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
+    size_t smem = pathgen_smem_bytes(a.one.m, a.max_slots, fp64);
+    auto kern = fp64 ? pathgen_perm_kernel<true> : pathgen_perm_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathgenThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * sm_count;
+    if (grid > a.total) grid = a.total;
+    kern<<<(unsigned)grid, kPathgenThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

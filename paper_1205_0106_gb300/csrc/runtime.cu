@@ -151,6 +151,31 @@ int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, 
     return AMC_OK;
 }
 
+// Paths from the paper's LCG-permuted unshifted points (one launch).
+int do_generate_permuted(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, cudaStream_t st) {
+    AMC_TRY(host_validate(o));
+    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_storage(S, ld, o->n_paths));
+    DevBridge *b;
+    AMC_TRY(get_bridge(c, o->n_steps, &b));
+    static thread_local PermArgs a;
+    memset(&a, 0, sizeof(PermArgs));
+    Job &J = a.one;
+    fill_job_common(o, &J);
+    J.nodes = prec == AMC_FP64 ? (const void *)b->nd : (const void *)b->nf;
+    J.nslots = b->nslots;
+    J.S = S;
+    J.ld = ld;
+    uint64_t M = 1;
+    host_lcg_params(o->seed, o->n_steps, o->n_paths, a.a, a.c, &M);
+    while ((1ull << a.log2M) < M) ++a.log2M;
+    a.V = c->V;
+    a.max_slots = b->nslots;
+    a.total = (o->n_paths + kTilePoints - 1) / kTilePoints;
+    AMC_TRY_CUDA(launch_pathgen_permuted(a, prec == AMC_FP64, c->sm_count, st));
+    return AMC_OK;
+}
+
 int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, bool greeks, double *res,
              cudaStream_t st, double *coef = nullptr) {
     AMC_TRY(host_validate(o));
@@ -653,6 +678,20 @@ int amc_generate_paths(amc_ctx *c, const amc_option *opt, int prec, void *S_dev,
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     return do_generate(c, opt, prec, S_dev, ld, (cudaStream_t)stream);
+}
+
+int amc_generate_paths_permuted(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, int64_t ld, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt) return AMC_EINVAL;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    return do_generate_permuted(c, opt, prec, S_dev, ld, (cudaStream_t)stream);
+}
+
+int amc_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uint32_t *c, uint64_t *M) {
+    if (n_dims < 1 || n_dims > AMC_MAX_STEPS || n_points < 1 || n_points > AMC_MAX_PATHS || !a || !c || !M)
+        return AMC_EINVAL;
+    host_lcg_params(seed, n_dims, n_points, a, c, M);
+    return AMC_OK;
 }
 
 int amc_sweep(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, int with_greeks,

@@ -45,6 +45,31 @@ int host_directions(int n_dims, uint32_t *V) {
 
 // Digital shift of dimension d: the high word of the d-th output of
 // SplitMix64 (Steele, Lea & Flood 2014) started from `seed`.
+// Parameters of the paper's LCG permutation of the quasi-random points
+// (§III.D): modulus M = least power of two >= n_points, per dimension
+// a_d = 4 (r_{2d} mod max(M/4, 1)) + 1 (a_d = 1 mod 4) and c_d = (r_{2d+1}
+// mod M) | 1 (odd), r_k the SplitMix64 outputs of the seed: a full-period
+// generator (Hull-Dobell), walked back into 0..n_points-1 by the kernel.
+void host_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uint32_t *c, uint64_t *M_out) {
+    uint64_t M = 1;
+    while ((int64_t)M < n_points) M <<= 1;
+    const uint64_t q = M >= 4 ? M / 4 : 1;
+    uint64_t x = seed;
+    auto next = [&]() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int d = 0; d < n_dims; ++d) {
+        const uint64_t r0 = next(), r1 = next();
+        a[d] = M == 1 ? 0u : (uint32_t)((4 * (r0 % q) + 1) % M);
+        c[d] = M == 1 ? 0u : (uint32_t)(((r1 % M) | 1u) % M);
+    }
+    *M_out = M;
+}
+
 void host_shifts(uint64_t seed, int n_dims, uint32_t *out) {
     uint64_t x = seed;
     for (int d = 0; d < n_dims; ++d) {

@@ -106,3 +106,17 @@ def test_sweep_plan_is_a_function_of_paths(amc):
     for prec in (amc.AMC_FP64, amc.AMC_MIXED):
         with pytest.raises(amc.AmcError):
             amc.amc_plan_sweep(2 ** 31, 152, prec, amc.AMC_RULE_LSM)
+
+
+@pytest.mark.parametrize("n", [1, 3, 1000, 12345, 2 ** 20])
+def test_library_lcg_permutation_parameters(amc, n):
+    """The library's LCG parameters (its own SplitMix64 stream) equal the
+    definition: a = 1 mod 4, c odd, M the least power of two >= n."""
+    import oracle
+    a, c, M = amc.amc_lcg_params(77, 40, n)
+    ao, co, Mo = oracle.lcg_params(77, 40, n)
+    assert M == Mo and M >= n and (M == 1 or M < 2 * n)
+    np.testing.assert_array_equal(a.astype(np.uint64), ao)
+    np.testing.assert_array_equal(c.astype(np.uint64), co)
+    if M >= 4:
+        assert np.all(a % 4 == 1) and np.all(c % 2 == 1)
