@@ -63,7 +63,8 @@ enum { AMC_FP64 = 0, AMC_MIXED = 1 };
 typedef struct amc_option {
     double S0, K, r, sigma, T; /* spot, strike, rate, volatility, maturity  */
     int32_t n_steps;           /* m exercise dates t_j = j T / m            */
-    int32_t basis;             /* LSM basis size p: {1, x, .., x^(p-1)}, x=S/K */
+    int32_t basis;             /* LSM basis size p: {1, y, .., y^(p-1)}, y = S/K - 1
+                                  (the span of {1, S, .., S^(p-1)})      */
     int64_t n_paths;           /* N Sobol' points / paths                   */
     int32_t type;              /* AMC_PUT or AMC_CALL                        */
     int32_t rule;              /* AMC_RULE_*                                 */
