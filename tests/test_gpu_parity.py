@@ -136,18 +136,60 @@ PRICE_CASES = [
     ("tiny_paths", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 10, 5, basis=3, seed=17)),
     ("deep_otm_degenerate", workloads.Option(200.0, 40.0, 0.06, 0.2, 1.0, 20, 2000, basis=3, seed=18)),
     ("big_group", workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 60, 2 ** 19 + 3, basis=4, seed=19)),
+    ("tiny_vol", workloads.Option(100.0, 100.0, 0.05, 0.01, 1.0, 50, 8192, basis=3, seed=20)),
+    ("huge_vol", workloads.Option(100.0, 100.0, 0.05, 1.5, 1.0, 50, 8192, basis=4, seed=21)),
+    ("zero_rate", workloads.Option(100.0, 105.0, 0.0, 0.3, 1.0, 50, 8192, basis=3, seed=22)),
+    ("negative_rate", workloads.Option(100.0, 95.0, -0.01, 0.25, 2.0, 40, 8192, basis=3, type=1, seed=23)),
+    ("short_maturity", workloads.Option(100.0, 100.0, 0.05, 0.3, 0.01, 10, 8192, basis=3, seed=24)),
+    ("deep_itm_put", workloads.Option(20.0, 40.0, 0.06, 0.2, 1.0, 50, 8192, basis=3, seed=25)),
+    ("long_call", workloads.Option(50.0, 60.0, 0.08, 0.4, 10.0, 120, 8192, basis=4, type=1, seed=26)),
 ]
+
+
+# LSM with a cubic over a very wide moneyness range is unstable at FP32
+# precision: the oracle's own price moves by more than 2e-4 K under path noise
+# at the FP32 paths' error level, and (volatility 150 %) under FP32 sums on
+# identical paths (tests/test_fp32_sensitivity.py).  These two cases keep the
+# 2e-4 K bar in FP64; in mixed precision no FP32 implementation can hold it.
+UNSTABLE_IN_FP32 = {"huge_vol", "long_call"}
 
 
 @pytest.mark.parametrize("name,opt", PRICE_CASES, ids=[c[0] for c in PRICE_CASES])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_price_vs_oracle(amc, ctx, name, opt, prec):
+    if prec == 1 and name in UNSTABLE_IN_FP32 and opt.rule == 0:
+        pytest.skip("LSM estimator unstable at FP32 precision (tests/test_fp32_sensitivity.py)")
     ref = _oracle_price(opt)
     got = _gpu_price(amc, ctx, opt, prec)
     assert got["status"] == 0
     assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
     assert got["degenerate_dates"] == ref["degenerate_dates"]
     assert abs(got["std_err"] - ref["std_err"]) <= 1e-3 * max(ref["std_err"], 1e-12) + 2e-4 * opt.K
+
+
+@pytest.mark.parametrize("name,opt", PRICE_CASES, ids=[c[0] for c in PRICE_CASES])
+def test_mixed_sweep_on_identical_paths(amc, ctx, torch, name, opt):
+    """The mixed sweep alone: the oracle's FP64 sweep run on the GPU's own
+    FP32 paths, so only the sweep arithmetic differs."""
+    if name in UNSTABLE_IN_FP32 and opt.rule == 0:
+        pytest.skip("LSM estimator unstable at FP32 precision (tests/test_fp32_sensitivity.py)")
+    ld = amc.amc_path_ld(opt.n_paths)
+    S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    amc.amc_generate_paths(ctx, opt, amc.AMC_MIXED, S)
+    amc.amc_sweep(ctx, opt, amc.AMC_MIXED, S, res)
+    torch.cuda.synchronize()
+    got = amc.res_to_dict(res.cpu().numpy())
+    Sh = S[:, :opt.n_paths].double().cpu().numpy()
+    if opt.rule == 0:
+        ref = oracle.lsm(Sh, opt.type, opt.K, opt.r, opt.T, opt.basis)
+    elif opt.rule == 1:
+        ref = oracle.paper_ub(Sh, opt.type, opt.S0, opt.K, opt.r, opt.sigma, opt.T)
+    else:
+        ref = oracle.european(Sh, opt.type, opt.K, opt.r, opt.T)
+    assert got["status"] == 0
+    assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+    assert got["degenerate_dates"] == ref["degenerate_dates"]
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])

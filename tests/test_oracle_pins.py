@@ -452,3 +452,4 @@ def test_permuted_points_give_an_unbiased_lsm_price():
     se = np.std([q["price"] for q in p_perm], ddof=1) / np.sqrt(len(p_perm))
     ref = oracle.price(36., 40., .06, .2, 1., 16, 2 ** 16, basis=3, seed=1)
     assert abs(mean - ref["price"]) < 4 * se + 3 * ref["std_err"] + 0.01
+
