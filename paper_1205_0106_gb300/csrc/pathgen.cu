@@ -6,14 +6,14 @@
 //   -> GBM in log space, S = S0 exp((r - sigma^2/2) t + sigma W)   Eq. 9
 //   -> date-major store S[j-1][i].
 //
-// One CTA of 128 threads owns a tile of 512 consecutive Sobol' points and
-// thread t the 4 consecutive points tile + 4t + q (q = 0..3), so every date
-// row is written with one 16-byte store per thread and the bridge stack is
-// read and written as float4.  The Gray code is linear over GF(2) and the
+// One CTA of kPathgenThreads threads owns a tile of 4 kPathgenThreads
+// consecutive Sobol' points and thread t the 4 consecutive points
+// tile + 4t + q (q = 0..3), so every date row is written with one 16-byte
+// store per thread and the bridge stack is read and written as float4.  The Gray code is linear over GF(2) and the
 // three index parts occupy disjoint bits, hence
 //   x(tile + 4t + q) = x(tile) xor x(4t) xor x(q):
 // x(tile) per dimension once per tile (shared memory), x(4t) from the
-// direction numbers v_2..v_9 selected by the thread's Gray bits, x(q) from
+// direction numbers v_2..v_(kGB+1) selected by the thread's Gray bits, x(q) from
 // v_1, v_2 (the same for all threads).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -214,6 +214,10 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
     }
 }
 
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+constexpr int kGB = ilog2(kTilePoints) - 1;       // Gray bits 1..kGB of the thread's point offset 4t
+static_assert((1 << ilog2(kTilePoints)) == kTilePoints && kGB + 1 < 12, "tile of 2^k points, direction numbers v_1..v_12");
+
 template <bool FP64>
 __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_constant__ KArgs a) {
     using Real = typename PG<FP64>::Real;
@@ -229,10 +233,10 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     const uint32_t *__restrict__ V = a.V;
     const int tid = threadIdx.x;
     const uint32_t t4 = 4u * (uint32_t)tid;
-    const uint32_t g4 = t4 ^ (t4 >> 1);                                   // Gray bits 1..8 of 4t
-    uint32_t gm[8];                                                       // all-ones where bit b+1 is set
+    const uint32_t g4 = t4 ^ (t4 >> 1);                                   // Gray bits 1..kGB of 4t
+    uint32_t gm[kGB];                                                     // all-ones where bit b+1 is set
 #pragma unroll
-    for (int b = 0; b < 8; ++b) gm[b] = 0u - ((g4 >> (b + 1)) & 1u);
+    for (int b = 0; b < kGB; ++b) gm[b] = 0u - ((g4 >> (b + 1)) & 1u);
     int cur = -1;
     int m = 0, nslots = 0;
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
@@ -272,15 +276,10 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
             const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];
+            const uint32_t vd[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
             uint32_t x0 = s_xb[nd.coord];
-            x0 ^= v0.y & gm[0];
-            x0 ^= v0.z & gm[1];
-            x0 ^= v0.w & gm[2];
-            x0 ^= v1.x & gm[3];
-            x0 ^= v1.y & gm[4];
-            x0 ^= v1.z & gm[5];
-            x0 ^= v1.w & gm[6];
-            x0 ^= v2.x & gm[7];
+#pragma unroll
+            for (int b = 0; b < kGB; ++b) x0 ^= vd[b + 1] & gm[b];
             const uint32_t xq[4] = {x0, x0 ^ v0.x, x0 ^ v0.x ^ v0.y, x0 ^ v0.y};
             const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
             const Real drift = mu_dt * (Real)nd.date;
