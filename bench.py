@@ -461,6 +461,18 @@ def run_amc(args):
             return total, sum(gen) / steps, sum(swp) / steps, res
         return ev[0].elapsed_time(ev[1]), None, None, res
 
+    if args.profile_batch:
+        bctx = amc.Context(local, arena_bytes=32 << 30)
+        opts = workloads.batch_options()
+        for _ in range(2):
+            amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+        if rank == 0:
+            print(json.dumps({"profile": "batch", "options": len(opts)}), flush=True)
+        bctx.close()
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile_paper:
         # profiling mode: the paper-rule sweep on resident paths (for ncu)
         popt = workloads.Option(**{**opt.as_dict(), "rule": workloads.RULE_PAPER_UB})
@@ -602,11 +614,13 @@ def main():
                     help="run only the boundary valuation launches (for ncu captures)")
     ap.add_argument("--profile-paper", action="store_true",
                     help="run only the paper-rule sweeps (for ncu captures)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run only the 4096-option batch, twice (for ncu launch lists)")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
-    if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper):
+    if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper or args.profile_batch):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
