@@ -69,6 +69,12 @@ def _lib():
         lib.orc_lcg_perm.restype = ctypes.c_uint64
         lib.orc_paths_permuted.argtypes = ([ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int64, _u32p, _u64p, _u64p,
                                                                     _dp])
+        lib.orc_dual_normal.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int64, ctypes.c_int]
+        lib.orc_dual_normal.restype = ctypes.c_double
+        lib.orc_dual_upper.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 4 +
+                                       [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _i32p, ctypes.c_int64,
+                                        ctypes.c_uint64, _dp, _dp])
         lib.orc_bs.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5
         lib.orc_bs.restype = ctypes.c_double
         lib.orc_solve_normal.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -259,6 +265,42 @@ def value_boundary(S, type_, K, r, T, beta, deg, details=False):
     if details:
         res["tau"] = tau
     return res
+
+
+def dual_normal(seed_in, m, n_in, i, j, k, s):
+    """Normal of inner step s of inner path k from date j of outer path i."""
+    return _lib().orc_dual_normal(seed_in, m, n_in, i, j, k, s)
+
+
+def dual_upper(S, type_, K, r, sigma, T, beta, deg, n_in, seed_in, details=False):
+    """Andersen-Broadie dual upper bound on the outer paths S for the boundary
+    (beta [m, p] in currency units, deg [m]); returns upper, std_err, L0."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    deg = np.ascontiguousarray(deg, dtype=np.int32)
+    m, N = S.shape
+    out = np.zeros(3)
+    U = np.zeros(N) if details else None
+    rc = _lib().orc_dual_upper(type_, K, r, sigma, T, m, N, beta.shape[1], _ptr(S, _dp), _ptr(beta, _dp),
+                               _ptr(deg, _i32p), n_in, seed_in, _ptr(out, _dp), _ptr(U, _dp))
+    if rc != 0:
+        raise ValueError("oracle dual_upper failed")
+    res = {"upper": out[0], "std_err": out[1], "L0": out[2]}
+    if details:
+        res["U"] = U
+    return res
+
+
+def price_dual(S0, K, r, sigma, T, n_steps, n_fit, n_outer, n_in, basis=3, type=PUT, seed=0, outer_seed=1,
+               seed_in=2):
+    """Boundary fitted on the points of `seed` (n_fit paths); on the n_outer
+    paths of outer_seed: the lower bound (the boundary applied) and the dual
+    upper bound with n_in inner paths per outer path and date."""
+    fit = lsm(paths(S0, r, sigma, T, n_steps, n_fit, seed), type, K, r, T, basis, details=True)
+    So = paths(S0, r, sigma, T, n_steps, n_outer, outer_seed)
+    low = value_boundary(So, type, K, r, T, fit["beta"], fit["deg"])
+    up = dual_upper(So, type, K, r, sigma, T, fit["beta"], fit["deg"], n_in, seed_in)
+    return fit, low, up
 
 
 def price_oos(S0, K, r, sigma, T, n_steps, n_paths, basis=3, type=PUT, seed=0, value_seed=1):

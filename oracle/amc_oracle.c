@@ -561,6 +561,119 @@ int orc_value_boundary(int type, double K, double r, double T, int m, int64_t N,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Dual upper bound of the Bermudan value for a given exercise boundary
+ * (Andersen & Broadie's primal-dual method; the duality of Rogers and of
+ * Haugh & Kogan that the paper's §IV lists among the methods for American
+ * options).  The policy: at date j < m exercise if h(S_j) > 0, the date is
+ * not degenerate and h(S_j) > c_j(y_j) (coefficients as in
+ * orc_value_boundary); at maturity take h(S_m).  On outer path i (paths S,
+ * discount factors to 0: D_j = e^{-r t_j}, Z_j = D_j h(S_j)):
+ *   Q_j  = continuation value at t_j, discounted to t_j: the mean over
+ *          n_in inner paths from S_j of the policy's payoff from t_{j+1} on,
+ *          discounted to t_j (j = 1..m-1);
+ *   L_j  = Z_j if the policy exercises at j, else D_j Q_j   (j = 1..m-1);
+ *   L_m  = Z_m;
+ *   M_0 = 0,  M_1 = L_1 - L0,  M_j = M_{j-1} + L_j - D_{j-1} Q_{j-1} (j >= 2),
+ *   with L0 = mean over the outer paths of L_1 (an estimate of E_0 L_1);
+ *   U_i = max_{j = 1..m} (Z_j - M_j);
+ * upper = mean U_i, std_err = sd(U_i)/sqrt(N); out[2] = L0.
+ * Inner path k from S_j: S <- S exp((r - sigma^2/2) dt + sigma sqrt(dt) z_s),
+ * s = 1, 2, .. until the policy stops or t_m; the normals z are the quantile
+ * of u = (x + 1/2) 2^-32, x the high 32 bits of output number
+ *   c + 1 = (((i m + j - 1) n_in + k) m + s - 1) + 1
+ * of SplitMix64(seed_in) (a counter-based stream: output n is the SplitMix64
+ * mix of seed_in + n 0x9E3779B97F4A7C15).                                   */
+static uint64_t orc_splitmix64_at(uint64_t seed, uint64_t n)
+{
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double orc_dual_normal(uint64_t seed_in, int m, int64_t n_in, int64_t i, int j, int64_t k, int s)
+{
+    uint64_t c = (((uint64_t)i * (uint64_t)m + (uint64_t)(j - 1)) * (uint64_t)n_in + (uint64_t)k) * (uint64_t)m
+                 + (uint64_t)(s - 1);
+    uint32_t x = (uint32_t)(orc_splitmix64_at(seed_in, c + 1) >> 32);
+    return orc_norm_icdf(orc_uniform(x));
+}
+
+static int orc_policy_stops(int type, double K, int p, const double *beta, const int32_t *deg, int j, int m,
+                            double S)
+{
+    if (j >= m) return 1;
+    if (deg[j - 1]) return 0;
+    double h = orc_payoff(type, S, K);
+    if (!(h > 0.0)) return 0;
+    double y = S / K - 1.0, c = 0.0, yk = 1.0;
+    for (int q = 0; q < p; ++q) { c += beta[(j - 1) * p + q] * yk; yk *= y; }
+    return h > c;
+}
+
+int orc_dual_upper(int type, double K, double r, double sigma, double T, int m, int64_t N, int p, const double *S,
+                   const double *beta, const int32_t *deg, int64_t n_in, uint64_t seed_in, double *out, double *Ui)
+{
+    double dt = T / m, disc = exp(-r * dt), drift = (r - 0.5 * sigma * sigma) * dt, vol = sigma * sqrt(dt);
+    double *Q = (double *)malloc(sizeof(double) * (size_t)(N * (m > 1 ? m - 1 : 1)));
+    double *U = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!Q || !U || p < 1 || p > 8) { free(Q); free(U); return -1; }
+    /* inner simulations: Q[i][j-1], discounted to t_j */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < N; ++i) {
+        for (int j = 1; j < m; ++j) {
+            double acc = 0.0;
+            for (int64_t k = 0; k < n_in; ++k) {
+                double x = S[(int64_t)(j - 1) * N + i], v = 0.0, dk = 1.0;
+                for (int s = 1; j + s <= m; ++s) {
+                    x = x * exp(drift + vol * orc_dual_normal(seed_in, m, n_in, i, j, k, s));
+                    dk *= disc;
+                    if (orc_policy_stops(type, K, p, beta, deg, j + s, m, x)) { v = dk * orc_payoff(type, x, K); break; }
+                }
+                acc += v;
+            }
+            Q[i * (m - 1) + (j - 1)] = acc / (double)n_in;
+        }
+    }
+    /* L0 = mean over the outer paths of L_1 */
+    double L0 = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double S1 = S[i], L1;
+        if (m == 1) L1 = disc * orc_payoff(type, S1, K);
+        else L1 = orc_policy_stops(type, K, p, beta, deg, 1, m, S1) ? disc * orc_payoff(type, S1, K)
+                                                                   : disc * Q[i * (m - 1)];
+        L0 += L1;
+    }
+    L0 /= (double)N;
+    double sum = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double Dj = 1.0, Mj = 0.0, best = -1e300, prevDQ = L0;
+        for (int j = 1; j <= m; ++j) {
+            Dj *= disc;
+            double Sj = S[(int64_t)(j - 1) * N + i], Zj = Dj * orc_payoff(type, Sj, K), Lj, DQ = 0.0;
+            if (j == m) Lj = Zj;
+            else {
+                DQ = Dj * Q[i * (m - 1) + (j - 1)];
+                Lj = orc_policy_stops(type, K, p, beta, deg, j, m, Sj) ? Zj : DQ;
+            }
+            Mj += Lj - prevDQ;
+            prevDQ = DQ;
+            if (Zj - Mj > best) best = Zj - Mj;
+        }
+        U[i] = best;
+        sum += best;
+    }
+    double mean = sum / (double)N, s2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) s2 += (U[i] - mean) * (U[i] - mean);
+    out[0] = mean;
+    out[1] = N > 1 ? sqrt(s2 / (double)(N - 1)) / sqrt((double)N) : 0.0;
+    out[2] = L0;
+    if (Ui) memcpy(Ui, U, sizeof(double) * (size_t)N);
+    free(Q); free(U);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The paper's own rule, Eqs. 10-11, written for calls and mirrored for
  * puts: on each path, V = max(h(S_{m-1}), BS(S_{m-1}, K, dt)) over the last
  * interval, then V = max(h(S_j), e^{-r dt} V) for j = m-2 .. 0 with

@@ -453,3 +453,99 @@ def test_permuted_points_give_an_unbiased_lsm_price():
     ref = oracle.price(36., 40., .06, .2, 1., 16, 2 ** 16, basis=3, seed=1)
     assert abs(mean - ref["price"]) < 4 * se + 3 * ref["std_err"] + 0.01
 
+
+
+# ------------------------------------------------ dual upper bound (primal-dual)
+def test_dual_normals_are_counter_based_splitmix64():
+    from scipy.special import ndtri
+    M64 = (1 << 64) - 1
+
+    def sm64_at(seed, n):
+        z = (seed + n * 0x9E3779B97F4A7C15) & M64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        return z ^ (z >> 31)
+
+    m, n_in = 7, 5
+    for (i, j, k, s) in [(0, 1, 0, 1), (3, 2, 4, 5), (11, 6, 2, 1)]:
+        c = ((i * m + j - 1) * n_in + k) * m + s - 1
+        x = sm64_at(9, c + 1) >> 32
+        assert oracle.dual_normal(9, m, n_in, i, j, k, s) == pytest.approx(ndtri((x + 0.5) / 2.0 ** 32), rel=1e-13)
+
+
+def test_dual_with_one_date_is_the_european_estimator():
+    S = oracle.paths(36.0, .06, .2, 1.0, 1, 3000, 4)
+    d = oracle.dual_upper(S, oracle.PUT, 40.0, .06, .2, 1.0, np.zeros((1, 3)), np.ones(1, dtype=np.int32), 8, 1,
+                          details=True)
+    eu = oracle.european(S, oracle.PUT, 40.0, .06, 1.0)["price"]
+    assert d["L0"] == pytest.approx(eu, rel=1e-13)
+    np.testing.assert_allclose(d["U"], eu, rtol=1e-13)
+
+
+def test_dual_matches_a_brute_force_loop():
+    """Pure-Python restatement on a tiny case: inner paths, L, M, max."""
+    import math
+    m, N, n_in, K, r, sig, T, seed_in = 3, 5, 3, 40.0, .06, .2, 1.0, 7
+    S = oracle.paths(36.0, r, sig, T, m, N, 3)
+    fit = oracle.lsm(oracle.paths(36.0, r, sig, T, m, 64, 1), oracle.PUT, K, r, T, 2, details=True)
+    beta, deg = fit["beta"], fit["deg"]
+    dt = T / m
+    h = lambda x: max(K - x, 0.0)
+
+    def stops(j, x):
+        if j >= m:
+            return True
+        if deg[j - 1] or not h(x) > 0:
+            return False
+        y = x / K - 1
+        return h(x) > sum(beta[j - 1][q] * y ** q for q in range(beta.shape[1]))
+
+    Q = np.zeros((N, m))
+    for i in range(N):
+        for j in range(1, m):
+            tot = 0.0
+            for k in range(n_in):
+                x, v = S[j - 1, i], 0.0
+                for s in range(1, m - j + 1):
+                    z = oracle.dual_normal(seed_in, m, n_in, i, j, k, s)
+                    x = x * math.exp((r - sig * sig / 2) * dt + sig * math.sqrt(dt) * z)
+                    if stops(j + s, x):
+                        v = math.exp(-r * s * dt) * h(x)
+                        break
+                tot += v
+            Q[i, j] = tot / n_in
+    L1 = [math.exp(-r * dt) * (h(S[0, i]) if stops(1, S[0, i]) else Q[i, 1]) for i in range(N)]
+    L0 = sum(L1) / N
+    U = []
+    for i in range(N):
+        Mj, prev, best = 0.0, L0, -1e300
+        for j in range(1, m + 1):
+            D = math.exp(-r * j * dt)
+            Z = D * h(S[j - 1, i])
+            if j == m:
+                L, DQ = Z, 0.0
+            else:
+                DQ = D * Q[i, j]
+                L = Z if stops(j, S[j - 1, i]) else DQ
+            Mj += L - prev
+            prev = DQ
+            best = max(best, Z - Mj)
+        U.append(best)
+    d = oracle.dual_upper(S, oracle.PUT, K, r, sig, T, beta, deg, n_in, seed_in, details=True)
+    assert d["L0"] == pytest.approx(L0, rel=1e-12)
+    np.testing.assert_allclose(d["U"], U, rtol=1e-12)
+
+
+def test_dual_and_lower_bound_bracket_the_bermudan_tree():
+    m = 10
+    fit, low, up = oracle.price_dual(36.0, 40.0, .06, .2, 1.0, m, 2 ** 13, 1024, 128, basis=3, seed=1, outer_seed=2,
+                                     seed_in=3)
+    tree = oracle.crr(oracle.PUT, 36, 40, .06, .2, 1.0, 10000, m, bermudan=True)
+    assert low["price"] <= tree + 3 * low["std_err"]
+    assert up["upper"] >= tree - 3 * up["std_err"]
+    assert up["upper"] - low["price"] < 0.03 * tree
+    # far below the perfect-foresight bound E[max_j Z_j] on the same outer paths
+    S = oracle.paths(36.0, .06, .2, 1.0, m, 1024, 2)
+    disc = np.exp(-.06 * np.arange(1, m + 1)[:, None] / m)
+    foresight = np.mean(np.max(disc * np.maximum(40.0 - S, 0.0), axis=0))
+    assert up["upper"] < foresight - 0.1
