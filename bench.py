@@ -122,9 +122,10 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def profile_traffic(kernel_src, summary):
-    """DRAM bytes per launch recorded in a committed ncu summary, or None when
-    the kernel source has changed since that capture (hash mismatch)."""
+def profile_traffic(kernel_src, summary, key="traffic_bytes_per_launch", conv=int):
+    """DRAM bytes per launch (or another `key: value` field) recorded in a
+    committed ncu summary, or None when the kernel source has changed since
+    that capture (hash mismatch)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, kernel_src), "rb") as f:
@@ -137,7 +138,7 @@ def profile_traffic(kernel_src, summary):
                     vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
         if vals.get("source_sha256_16") != h:
             return None
-        return int(vals["traffic_bytes_per_launch"])
+        return conv(vals[key])
     except Exception:
         return None
 
@@ -278,6 +279,63 @@ def paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warm
                                                     "profiles/sweep_pathwise_paper_2p20x252_mixed.md"),
                          "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
             "price": got["price"], "workload": "Eqs. 10-11 on the 2^20 x 252 paths of shift seed 2"}
+
+
+DUAL_OUTER, DUAL_INNER = 4096, 128
+DUAL_SMS, DUAL_SM_MHZ = 152, 2070.0          # GB300 SMs, maximum SM clock
+
+
+def dual_setup(amc, ctx, torch, stream, opt):
+    """Boundary fitted on the bench workload's points; 4096 outer paths of
+    shift seed opt.seed + 11 (mixed precision).  Returns (S, coef, outer)."""
+    S, coef, _, _ = oos_setup(amc, ctx, torch, stream, opt, opt.seed + 5)
+    del S
+    outer = workloads.Option(**{**opt.as_dict(), "n_paths": DUAL_OUTER, "seed": opt.seed + 11})
+    So = torch.empty((opt.n_steps, amc.amc_path_ld(DUAL_OUTER)), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        amc.amc_generate_paths(ctx, outer, amc.AMC_MIXED, So, stream=stream)
+    stream.synchronize()
+    return So, coef, outer
+
+
+def dual_bench(amc, ctx, torch, stream, opt, reps=5, warmup=2):
+    """Dual upper bound of the bench workload's fitted boundary on 4096 outer
+    paths with 128 inner paths per outer path and date: the inner-simulation
+    kernel and its reduction timed with CUDA events on their stream; the
+    lower bound (the boundary applied to the same outer paths) beside it."""
+    So, coef, outer = dual_setup(amc, ctx, torch, stream, opt)
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    low = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        amc.amc_value_boundary(ctx, outer, amc.AMC_MIXED, So, coef, low, stream=stream)
+        for _ in range(warmup):
+            amc.amc_dual_upper(ctx, outer, amc.AMC_MIXED, So, coef, DUAL_INNER, 13, res, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            amc.amc_dual_upper(ctx, outer, amc.AMC_MIXED, So, coef, DUAL_INNER, 13, res, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    r, lo = res.cpu().numpy(), amc.res_to_dict(low.cpu().numpy())
+    steps = float(r[7])
+    # issue-slot roofline: warp instructions per inner step from the committed
+    # ncu capture x steps/s, against 152 SMs x 4 schedulers x 1 issue/clock
+    summary = "profiles/dual_inner_2p20x252_4096x128_mixed.md"
+    ipstep = profile_traffic("paper_1205_0106_gb300/csrc/dual.cu", summary, "warp_instr_per_inner_step", float)
+    peak = DUAL_SMS * 4 * DUAL_SM_MHZ * 1e6
+    achieved = None if ipstep is None else ipstep * steps / (ms * 1e-3)
+    rl = {"bound": "alu", "unit": "warp-instr/s", "achieved": achieved, "peak": peak,
+          "frac": None if achieved is None else achieved / peak,
+          "traffic": profile_traffic("paper_1205_0106_gb300/csrc/dual.cu", summary),
+          "peak_kind": "issue slots at the maximum SM clock", "warp_instr_per_inner_step": ipstep}
+    return {"kernel": "dual_inner_kernel + dual_final_kernel", "ms": ms, "inner_steps": steps,
+            "value": steps / (ms * 1e-3), "unit": "inner path-steps/s", "roofline": rl,
+            "upper": float(r[0]), "upper_std_err": float(r[1]), "L0": float(r[6]),
+            "lower": lo["price"], "lower_std_err": lo["std_err"], "gap": float(r[0]) - lo["price"],
+            "workload": "boundary fitted on the 2^20 x 252 paths of shift seed 2; 4096 outer paths of shift "
+                        "seed 13, 128 inner paths per outer path and date, inner seed 13"}
 
 
 def fig1_bench(amc, device):
@@ -502,6 +560,21 @@ def run_amc(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    if args.profile_dual:
+        # profiling mode: fit once, outer paths, then only the dual launches (for ncu)
+        So, coef, outer = dual_setup(amc, ctx, torch, stream, opt)
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup + args.steps):
+                amc.amc_dual_upper(ctx, outer, amc.AMC_MIXED, So, coef, DUAL_INNER, 13, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "dual", "steps": args.steps, "warmup": args.warmup,
+                              "inner_steps": float(res[7].item())}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile:
         # profiling mode: only the timed mixed-precision steps (for ncu)
         t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
@@ -577,6 +650,7 @@ def run_amc(args):
         line["oos"] = oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
         line["paper_rule"] = paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
         line["randomization"] = randomization_bench(amc, ctx, torch, stream, opt)
+        line["dual"] = dual_bench(amc, ctx, torch, stream, opt)
     if args.serve_seconds > 0:
         times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
         sctx = amc.Context(local, arena_bytes=24 << 30)
@@ -616,11 +690,14 @@ def main():
                     help="run only the paper-rule sweeps (for ncu captures)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only the 4096-option batch, twice (for ncu launch lists)")
+    ap.add_argument("--profile-dual", action="store_true",
+                    help="fit the boundary, then run only two dual upper-bound launches (for ncu captures)")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
-    if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper or args.profile_batch):
+    if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper or args.profile_batch
+                                or args.profile_dual):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

@@ -195,6 +195,34 @@ int amc_fit_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *
 int amc_value_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
                        int64_t ld, const double *coef_dev, double *res_dev, void *stream);
 
+/* Dual upper bound of a fitted boundary (the dual formulation of §IV,
+ * ref. [11], with the Andersen-Broadie martingale of the boundary).  On each
+ * outer path i of S (an AMC_RULE_LSM option's paths, as amc_sweep) and for
+ * each date t_j < T, n_inner inner paths start from S_j(i), move by the exact
+ * GBM step of Eq. 9 and stop at the first later date where the boundary
+ * coef_dev exercises (as amc_value_boundary; always at t_m); Q_j(i) is the
+ * mean of their payoffs discounted to t_j.  With D_j = e^{-r t_j},
+ * Z_j = D_j h(S_j), L_j = Z_j where the boundary exercises at t_j and D_j Q_j
+ * elsewhere (L_m = Z_m), L0 = mean over i of L_1, and
+ * M_j = sum_{l<=j} (L_l - D_{l-1} Q_{l-1}) with D_0 Q_0 = L0:
+ * U(i) = max_{j=1..m} (Z_j - M_j).  res_dev = [mean U, std_err of U, 0, 0,
+ * flagged dates, status, L0, inner steps simulated]; U_dev[n_paths]
+ * (device, 8-byte aligned,
+ * may be null) receives U(i).  The inner normal of step s (1-based, to date
+ * j + s) of inner path k (0-based) from date j of outer path i (0-based) is
+ * Phi^-1((x + 1/2) 2^-32), x the high 32 bits of SplitMix64 output number
+ * n = ((i m + j - 1) n_inner + k) m + s of inner_seed, that is
+ * mix(inner_seed + n 0x9E3779B97F4A7C15).  FP32 inner paths under
+ * AMC_MIXED (FP64 sums), all FP64 under AMC_FP64.  AMC_EINVAL for a rule
+ * other than AMC_RULE_LSM, n_inner < 1 or > AMC_DUAL_MAX_INNER,
+ * n_paths > 2^31 - 1, misaligned pointers, or more than AMC_DUAL_MAX_WORK
+ * possible inner steps (n_paths n_inner m (m-1) / 2).  Asynchronous.      */
+#define AMC_DUAL_MAX_WORK (1LL << 40)
+#define AMC_DUAL_MAX_INNER (1LL << 30)
+int amc_dual_upper(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev, int64_t ld,
+                   const double *coef_dev, int64_t n_inner, uint64_t inner_seed, double *res_dev,
+                   double *U_dev, void *stream);
+
 /* --------------------------------------------------- host-level calls */
 /* Price one option (paths in the context arena), blocking; out on host.   */
 int amc_price_american(amc_ctx *ctx, double S0, double K, double r, double sigma,
@@ -212,6 +240,14 @@ int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
  * (result into value).                                                     */
 int amc_price_oos(amc_ctx *ctx, const amc_option *opt, uint64_t value_seed, int prec,
                   amc_result *fit, amc_result *value);
+/* Lower and upper bounds of the Bermudan value, blocking: the boundary is
+ * fitted on the points of opt->seed (in-sample result into fit, may be
+ * null); on n_outer independent paths of outer_seed it is applied
+ * (amc_value_boundary, into lower, may be null) and its dual upper bound
+ * taken with n_inner inner paths per outer path and date (amc_dual_upper,
+ * into upper).                                                             */
+int amc_price_dual(amc_ctx *ctx, const amc_option *opt, uint64_t outer_seed, int64_t n_outer, int64_t n_inner,
+                   uint64_t inner_seed, int prec, amc_result *fit, amc_result *lower, amc_result *upper);
 /* Price, delta and vega of n options (frozen-boundary pathwise adjoint).   */
 int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                double *price, double *delta, double *vega);

@@ -23,6 +23,8 @@ AMC_RULE_LSM, AMC_RULE_PAPER_UB, AMC_RULE_EUROPEAN = 0, 1, 2
 AMC_FP64, AMC_MIXED = 0, 1
 AMC_RES_DOUBLES = 8
 AMC_COEF_STRIDE = 5
+AMC_DUAL_MAX_WORK = 1 << 40
+AMC_DUAL_MAX_INNER = 1 << 30
 AMC_MAX_STEPS = 512
 
 
@@ -90,6 +92,8 @@ SIGNATURES = {
     "amc_fit_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_value_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_price_oos": (ctypes.c_int, [_vp, _optp, _u64, ctypes.c_int, _resp, _resp]),
+    "amc_dual_upper": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _i64, _u64, _vp, _vp, _vp]),
+    "amc_price_dual": (ctypes.c_int, [_vp, _optp, _u64, _i64, _i64, _u64, ctypes.c_int, _resp, _resp, _resp]),
     "amc_price_american": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _u64,
                                           ctypes.c_int, ctypes.c_int, _resp]),
@@ -318,6 +322,26 @@ def amc_price_oos(ctx, opt, value_seed, prec=AMC_MIXED):
     _check(lib().amc_price_oos(ctx.handle, ctypes.byref(make_option(opt)), value_seed, prec, ctypes.byref(fit),
                                ctypes.byref(val)), "amc_price_oos")
     return _res_dict(fit), _res_dict(val)
+
+
+def amc_dual_upper(ctx, opt, prec, S, coef, n_inner, inner_seed, res, U=None, ld=None, stream=None):
+    """Dual upper bound of the boundary coef on the outer paths S: res =
+    [mean U, std_err, 0, 0, flagged dates, status, L0, inner steps]; U (device, may
+    be None) receives the per-path upper values."""
+    ld = S.shape[1] if ld is None else ld
+    _check(lib().amc_dual_upper(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(S), ld, _ptr(coef), n_inner,
+                                inner_seed, _ptr(res), _ptr(U), _stream(stream)), "amc_dual_upper")
+
+
+def amc_price_dual(ctx, opt, outer_seed, n_outer, n_inner, inner_seed, prec=AMC_MIXED):
+    """Boundary fitted on opt's points; on n_outer paths of outer_seed its
+    value (lower bound) and its dual upper bound.  Returns (fit, lower,
+    upper) result dicts."""
+    fit, low, up = amc_result(), amc_result(), amc_result()
+    _check(lib().amc_price_dual(ctx.handle, ctypes.byref(make_option(opt)), outer_seed, n_outer, n_inner,
+                                inner_seed, prec, ctypes.byref(fit), ctypes.byref(low), ctypes.byref(up)),
+           "amc_price_dual")
+    return _res_dict(fit), _res_dict(low), _res_dict(up)
 
 
 # ------------------------------------------------------------ serving

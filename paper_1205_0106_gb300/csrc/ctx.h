@@ -63,6 +63,8 @@ struct amc_ctx {
     int32_t *status1 = nullptr;
     double *finv = nullptr;                          // per-CTA sums of the boundary valuation (grown on demand)
     int64_t finv_ctas = 0;
+    double *dualw = nullptr;                         // per-path L_1, V and inner steps of the dual upper bound (grown on demand)
+    int64_t dualw_n = 0;
     uint64_t *xch1 = nullptr;                        // exchange units of the mixed LSM sweep
     uint32_t epoch = 0;                              // launch tag of those units
     int gcap = 0;

@@ -151,4 +151,20 @@ int64_t value_ctas(int64_t n_paths);            // CTAs of the boundary valuatio
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 
+// Dual upper bound of a fitted boundary (dual.cu): the option, its outer
+// paths S [m][ld], boundary coef, result block and status word in `one`.
+struct DualArgs {
+    Job one;
+    int64_t n_in;                   // inner paths per outer path and date
+    uint64_t seed_in;               // counter-based SplitMix64 seed of the inner normals
+    double *L1;                     // [N] L_1 per outer path (scratch)
+    double *V;                      // [N] max_j (Z_j - M_j - L0) per outer path (scratch)
+    double *W;                      // [N] inner steps simulated per outer path (scratch)
+    double *U;                      // [N] U = L0 + V per outer path, or null
+};
+constexpr int kDualThreads = 256;           // inner simulations: up to 8 warps per outer path
+constexpr int kDualFinalThreads = 1024;
+size_t dual_smem(int m, bool fp64);
+cudaError_t launch_dual_upper(const DualArgs &a, bool fp64, cudaStream_t st);
+
 }  // namespace amc

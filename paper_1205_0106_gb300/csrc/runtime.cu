@@ -255,6 +255,43 @@ int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     return AMC_OK;
 }
 
+int do_dual(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, const double *coef, int64_t n_in,
+            uint64_t seed_in, double *res, double *U, cudaStream_t st) {
+    AMC_TRY(host_validate(o));
+    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_storage(S, ld, o->n_paths));
+    if (o->rule != AMC_RULE_LSM || !coef || ((uintptr_t)coef & 7u) != 0 || !res || ((uintptr_t)res & 7u) != 0 ||
+        ((uintptr_t)U & 7u) != 0 || n_in < 1 || n_in > AMC_DUAL_MAX_INNER || o->n_paths > INT32_MAX)
+        return AMC_EINVAL;
+    const double m = o->n_steps;
+    if ((double)o->n_paths * (double)n_in * m * (m - 1.0) * 0.5 > (double)AMC_DUAL_MAX_WORK) return AMC_EINVAL;
+    DualArgs a;
+    memset(&a, 0, sizeof(a));
+    Job &J = a.one;
+    fill_job_common(o, &J);
+    J.S = const_cast<void *>(S);
+    J.ld = ld;
+    J.coef = const_cast<double *>(coef);
+    J.res = res;
+    J.status = c->status1;
+    if (o->n_paths > c->dualw_n) {                    // grown on demand (synchronises the device once)
+        cudaFree(c->dualw);
+        c->dualw = nullptr;
+        c->dualw_n = 0;
+        if (cudaMalloc(&c->dualw, sizeof(double) * 3 * (size_t)o->n_paths) != cudaSuccess) return AMC_ENOMEM;
+        c->dualw_n = o->n_paths;
+    }
+    a.n_in = n_in;
+    a.seed_in = seed_in;
+    a.L1 = c->dualw;
+    a.V = c->dualw + o->n_paths;
+    a.W = c->dualw + 2 * o->n_paths;
+    a.U = U;
+    AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
+    AMC_TRY_CUDA(launch_dual_upper(a, prec == AMC_FP64, st));
+    return AMC_OK;
+}
+
 amc_option make_option(double S0, double K, double r, double sigma, double T, int n_steps, int64_t n_paths,
                        int basis, int type, uint64_t seed, int rule) {
     amc_option o;
@@ -624,6 +661,7 @@ int amc_ctx_destroy(amc_ctx *c) {
     cudaFree(c->arrive1);
     cudaFree(c->fin1);
     cudaFree(c->finv);
+    cudaFree(c->dualw);
     cudaFree(c->res1);
     cudaFree(c->status1);
     cudaFree(c->xch1);
@@ -756,6 +794,50 @@ int amc_price_oos(amc_ctx *c, const amc_option *opt, uint64_t value_seed, int pr
     else if ((int32_t)h[5] != 0) s1 = (int32_t)h[5];
     int s2 = result_from(h + AMC_RES_DOUBLES, value);
     return s1 != AMC_OK ? s1 : s2;
+}
+
+int amc_dual_upper(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, const double *coef_dev,
+                   int64_t n_inner, uint64_t inner_seed, double *res_dev, double *U_dev, void *stream) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt) return AMC_EINVAL;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    return do_dual(c, opt, prec, S_dev, ld, coef_dev, n_inner, inner_seed, res_dev, U_dev, (cudaStream_t)stream);
+}
+
+int amc_price_dual(amc_ctx *c, const amc_option *opt, uint64_t outer_seed, int64_t n_outer, int64_t n_inner,
+                   uint64_t inner_seed, int prec, amc_result *fit, amc_result *lower, amc_result *upper) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt || !upper || opt->rule != AMC_RULE_LSM) return AMC_EINVAL;
+    amc_option ov = *opt;
+    ov.seed = outer_seed;
+    ov.n_paths = n_outer;
+    AMC_TRY(host_validate(opt));
+    AMC_TRY(host_validate(&ov));
+    AMC_TRY(check_prec(prec));
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    c->arena_top = 0;
+    const size_t es = prec == AMC_FP64 ? 8 : 4;
+    const int64_t ld = host_ld(opt->n_paths), ldo = host_ld(n_outer);
+    const size_t bytes = (size_t)opt->n_steps * es * (size_t)(ld > ldo ? ld : ldo);
+    void *S;
+    double *coef, *res3;
+    AMC_TRY(arena_alloc(c, bytes, &S));               // fitting paths, then (stream-ordered) the outer paths
+    AMC_TRY(arena_alloc(c, sizeof(double) * kCoefStride * opt->n_steps, (void **)&coef));
+    AMC_TRY(arena_alloc(c, sizeof(double) * 3 * AMC_RES_DOUBLES, (void **)&res3));
+    cudaStream_t st = c->stream;
+    AMC_TRY(do_generate(c, opt, prec, S, ld, st));
+    AMC_TRY(do_sweep(c, opt, prec, S, ld, false, res3, st, coef));
+    AMC_TRY(do_generate(c, &ov, prec, S, ldo, st));
+    AMC_TRY(do_value(c, &ov, prec, S, ldo, coef, res3 + AMC_RES_DOUBLES, st));
+    AMC_TRY(do_dual(c, &ov, prec, S, ldo, coef, n_inner, inner_seed, res3 + 2 * AMC_RES_DOUBLES, nullptr, st));
+    double h[3 * AMC_RES_DOUBLES];
+    AMC_TRY_CUDA(cudaMemcpyAsync(h, res3, sizeof(h), cudaMemcpyDeviceToHost, st));
+    AMC_TRY_CUDA(cudaStreamSynchronize(st));
+    amc_result tmp;
+    const int s1 = result_from(h, fit ? fit : &tmp);
+    const int s2 = result_from(h + AMC_RES_DOUBLES, lower ? lower : &tmp);
+    const int s3 = result_from(h + 2 * AMC_RES_DOUBLES, upper);
+    return s1 != AMC_OK ? s1 : (s2 != AMC_OK ? s2 : s3);
 }
 
 int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, double T, int n_steps,
