@@ -167,6 +167,19 @@ def cpu_baseline(opt, n_sample=None):
     out = {"value": n_sample * opt.n_steps / dt, "unit": METRIC, "cores": oracle.threads(), "kind": "oracle",
            "sample": "first %d of %d paths, all %d dates, paths + LSM sweep, %.1f s" % (
                n_sample, opt.n_paths, opt.n_steps, dt)}
+    # the same on one core, on the first 2^12 paths
+    cores = oracle.threads()
+    n1 = min(n_sample, 1 << 12)
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        S = oracle.paths(opt.S0, opt.r, opt.sigma, opt.T, opt.n_steps, n1, opt.seed)
+        oracle.lsm(S, opt.type, opt.K, opt.r, opt.T, opt.basis)
+        dt1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(cores)
+    out["value_1core"] = n1 * opt.n_steps / dt1
+    out["sample_1core"] = "first %d paths, all %d dates, one thread, %.2f s" % (n1, opt.n_steps, dt1)
     return out, (res["price"] if n_sample == opt.n_paths else None)
 
 
@@ -285,6 +298,19 @@ DUAL_OUTER, DUAL_INNER = 4096, 128
 DUAL_SMS, DUAL_SM_MHZ = 152, 2070.0          # GB300 SMs, maximum SM clock
 
 
+def issue_roofline(kernel_src, summary, units_per_s):
+    """Issue-slot roofline of a kernel: warp instructions per unit of work
+    from its committed ncu capture (hash-checked) x the units per second
+    timed by CUDA events, against 152 SMs x 4 schedulers x 1 warp
+    instruction per clock at the maximum SM clock."""
+    per_unit = profile_traffic(kernel_src, summary, "warp_instr_per_unit", float)
+    peak = DUAL_SMS * 4 * DUAL_SM_MHZ * 1e6
+    achieved = None if per_unit is None else per_unit * units_per_s
+    return {"bound": "alu", "unit": "warp-instr/s", "achieved": achieved, "peak": peak,
+            "frac": None if achieved is None else achieved / peak, "warp_instr_per_unit": per_unit,
+            "peak_kind": "issue slots at the maximum SM clock"}
+
+
 def dual_setup(amc, ctx, torch, stream, opt):
     """Boundary fitted on the bench workload's points; 4096 outer paths of
     shift seed opt.seed + 11 (mixed precision).  Returns (S, coef, outer)."""
@@ -323,13 +349,8 @@ def dual_bench(amc, ctx, torch, stream, opt, reps=5, warmup=2):
     # issue-slot roofline: warp instructions per inner step from the committed
     # ncu capture x steps/s, against 152 SMs x 4 schedulers x 1 issue/clock
     summary = "profiles/dual_inner_2p20x252_4096x128_mixed.md"
-    ipstep = profile_traffic("paper_1205_0106_gb300/csrc/dual.cu", summary, "warp_instr_per_inner_step", float)
-    peak = DUAL_SMS * 4 * DUAL_SM_MHZ * 1e6
-    achieved = None if ipstep is None else ipstep * steps / (ms * 1e-3)
-    rl = {"bound": "alu", "unit": "warp-instr/s", "achieved": achieved, "peak": peak,
-          "frac": None if achieved is None else achieved / peak,
-          "traffic": profile_traffic("paper_1205_0106_gb300/csrc/dual.cu", summary),
-          "peak_kind": "issue slots at the maximum SM clock", "warp_instr_per_inner_step": ipstep}
+    rl = issue_roofline("paper_1205_0106_gb300/csrc/dual.cu", summary, steps / (ms * 1e-3))
+    rl["traffic"] = profile_traffic("paper_1205_0106_gb300/csrc/dual.cu", summary)
     return {"kernel": "dual_inner_kernel + dual_final_kernel", "ms": ms, "inner_steps": steps,
             "value": steps / (ms * 1e-3), "unit": "inner path-steps/s", "roofline": rl,
             "upper": float(r[0]), "upper_std_err": float(r[1]), "L0": float(r[6]),
@@ -628,10 +649,14 @@ def run_amc(args):
                 "traffic": profile_traffic("paper_1205_0106_gb300/csrc/sweep_v2.cu",
                                            "profiles/sweep_lsm_v2_2p20x252_mixed.md"),
                 "kernel": "sweep_lsm_v2_kernel", "ms": sweep_ms, "peak_kind": peak_kind,
-                "algorithmic_bytes": bytes_sweep}
+                "algorithmic_bytes": bytes_sweep,
+                "issue": issue_roofline("paper_1205_0106_gb300/csrc/sweep_v2.cu",
+                                        "profiles/sweep_lsm_v2_2p20x252_mixed.md", units / (sweep_ms * 1e-3))}
     rl_gen = {"bound": "hbm", "achieved": gen_gbs, "peak": hbm, "unit": "GB/s", "frac": gen_gbs / hbm,
               "traffic": profile_traffic("paper_1205_0106_gb300/csrc/pathgen.cu", "profiles/pathgen_2p20x252_mixed.md"),
               "kernel": "pathgen_kernel", "ms": gen_ms, "peak_kind": peak_kind, "algorithmic_bytes": bytes_gen,
+              "issue": issue_roofline("paper_1205_0106_gb300/csrc/pathgen.cu", "profiles/pathgen_2p20x252_mixed.md",
+                                      units / (gen_ms * 1e-3)),
               "note": "issue-bound (ALU); the HBM write fraction is the secondary bound"}
     dominant = rl_gen if gen_ms >= sweep_ms else rl_sweep
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,

@@ -89,6 +89,8 @@ def _lib():
         lib.orc_crr.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int] * 3
         lib.orc_crr.restype = ctypes.c_double
         lib.orc_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         _LIB = lib
     return _LIB
 
@@ -113,6 +115,11 @@ def joe_kuo_raw(m):
 def threads():
     """Threads the oracle's OpenMP loops use."""
     return _lib().orc_threads()
+
+
+def set_threads(n):
+    """Sets the threads of the oracle's OpenMP loops."""
+    _lib().orc_set_threads(int(n))
 
 
 def splitmix64(seed, n):

@@ -50,6 +50,16 @@ int orc_threads(void)
 #endif
 }
 
+/* Sets the threads of the oracle's parallel loops (no effect without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 #define ORC_PUT 0
 #define ORC_CALL 1
 

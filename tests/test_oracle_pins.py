@@ -549,3 +549,24 @@ def test_dual_and_lower_bound_bracket_the_bermudan_tree():
     disc = np.exp(-.06 * np.arange(1, m + 1)[:, None] / m)
     foresight = np.mean(np.max(disc * np.maximum(40.0 - S, 0.0), axis=0))
     assert up["upper"] < foresight - 0.1
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    """OpenMP runs only across independent paths; sums are taken in a fixed
+    order, so one thread and all threads give the same bits."""
+    n0 = oracle.threads()
+    S = oracle.paths(36.0, .06, .2, 1.0, 12, 3001, 5)
+    fit = oracle.lsm(S, oracle.PUT, 40.0, .06, 1.0, 3, details=True)
+    d = oracle.dual_upper(S[:, :40], oracle.PUT, 40.0, .06, .2, 1.0, fit["beta"], fit["deg"], 16, 3)
+    try:
+        oracle.set_threads(1)
+        assert oracle.threads() == 1
+        S1 = oracle.paths(36.0, .06, .2, 1.0, 12, 3001, 5)
+        fit1 = oracle.lsm(S1, oracle.PUT, 40.0, .06, 1.0, 3, details=True)
+        d1 = oracle.dual_upper(S1[:, :40], oracle.PUT, 40.0, .06, .2, 1.0, fit1["beta"], fit1["deg"], 16, 3)
+    finally:
+        oracle.set_threads(n0)
+    assert oracle.threads() == n0
+    assert np.array_equal(S, S1)
+    assert fit["price"] == fit1["price"] and np.array_equal(fit["beta"], fit1["beta"])
+    assert d == d1
