@@ -1,0 +1,81 @@
+"""Sensitivity of the LSM estimator to FP32 arithmetic, measured with the
+oracle (test helper, CPU): its price under path noise at the FP32 paths'
+error level, and under FP32 sums in the sweep's order.  Written in numpy
+from the sweep's definition (oracle paths and solve)."""
+import numpy as np
+
+import oracle
+
+
+def paths(o):
+    return oracle.paths(o.S0, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.seed)
+
+
+def path_noise_spread(o, eps=2e-5, reps=4):
+    S = paths(o)
+    ref = oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"]
+    return max(abs(oracle.lsm(S * (1 + eps * np.random.default_rng(k).standard_normal(S.shape)), o.type, o.K, o.r,
+                              o.T, o.basis)["price"] - ref) / o.K for k in range(reps))
+
+
+def lsm_fp32_sums(S, o):
+    """LSM (units of K, moneyness basis) with FP32 cash flows and FP32
+    per-thread (8 paths) + pairwise sums of the moments and right-hand
+    sides, the FP64 solve of the oracle."""
+    m, N = S.shape
+    p, put = o.basis, o.type == oracle.PUT
+    disc = np.float32(np.exp(-o.r * o.T / m))
+    y_all = (S / o.K - 1.0).astype(np.float32)
+    h_all = np.maximum(-y_all if put else y_all, np.float32(0))
+    cf = h_all[m - 1].copy()
+
+    def fsum(v):
+        v = np.concatenate([v.astype(np.float32), np.zeros((-len(v)) % 8, np.float32)]).reshape(-1, 8)
+        acc = np.zeros(v.shape[0], np.float32)
+        for k in range(8):
+            acc = acc + v[:, k]
+        while len(acc) > 1:
+            acc = np.concatenate([acc, np.zeros(len(acc) % 2, np.float32)])
+            acc = acc[0::2] + acc[1::2]
+        return float(acc[0]) if len(acc) else 0.0
+
+    for j in range(m - 2, -1, -1):
+        cf = cf * disc
+        itm = h_all[j] > 0
+        yy = y_all[j][itm]
+        if yy.size < p:
+            continue
+        pw = [np.ones_like(yy)]
+        for k in range(1, 2 * p - 1):
+            pw.append(pw[-1] * yy)
+        G = np.array([[fsum(pw[a + b]) for b in range(p)] for a in range(p)])
+        beta = oracle.solve_normal(G, np.array([fsum(cf[itm] * pw[k]) for k in range(p)]))
+        if beta is None:
+            continue
+        cont = sum(np.float32(beta[k]) * pw[k] for k in range(p))
+        ex = h_all[j][itm] > cont
+        c = cf[itm]
+        c[ex] = h_all[j][itm][ex]
+        cf[itm] = c
+    return float(np.exp(-o.r * o.T / m) * np.mean(cf.astype(np.float64)))
+
+
+def fp32_sum_shift(o):
+    S = paths(o)
+    ref = oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"] / o.K
+    return abs(lsm_fp32_sums(S, o) - ref)
+
+
+def check_mixed_vs_oracle(o, got, ref, fp64_price, bar=2e-4):
+    """A mixed-precision price `got` against the oracle's `ref` on the same
+    points: within bar K; or, where the oracle's own price moves by more than
+    half the bar under FP32-level path noise or FP32 sums (LSM unstable at
+    FP32 precision on this option), within three times that movement, and
+    the FP64 GPU price (fp64_price(), called only then) within bar K."""
+    err = abs(got - ref) / o.K
+    if err <= bar:
+        return
+    spread = max(path_noise_spread(o, reps=2), fp32_sum_shift(o))
+    assert spread > bar / 2, ("mixed price off the oracle on an FP32-stable option", o, got, ref, spread)
+    assert err <= 3 * spread, (o, got, ref, spread)
+    assert abs(fp64_price() - ref) <= bar * o.K, (o, ref)

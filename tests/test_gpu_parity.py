@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import workloads
+from lsm_sensitivity import check_mixed_vs_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -217,6 +218,46 @@ def test_batch_equals_single(amc, ctx):
         for o, b in zip(opts, batch):
             s = _gpu_price(amc, ctx, o, prec)
             assert b["price"] == s["price"] and b["std_err"] == s["std_err"], (o, b, s)
+
+
+def test_full_batch_sampled_vs_oracle_and_alone(amc, ctx):
+    """The 4096-option batch at full size (2^14..2^18 paths, 12..365 dates),
+    mixed precision: a seeded sample of 16 options equals the option priced
+    alone bit for bit, and a seeded 1 % sample is within 2e-4 K of the
+    oracle on the same points, with equal degenerate counts.  Options on
+    which LSM is unstable at FP32 precision (deep in-the-money calls with a
+    wide moneyness range) are held to the oracle's own FP32 sensitivity, and
+    their FP64 GPU price to 2e-4 K (check_mixed_vs_oracle)."""
+    opts = workloads.batch_options()
+    res = amc.amc_price_batch(ctx, opts, amc.AMC_MIXED)
+    assert all(r["status"] == 0 for r in res)
+    for i in np.random.default_rng(43).choice(len(opts), size=16, replace=False):
+        s = _gpu_price(amc, ctx, opts[i], amc.AMC_MIXED)
+        assert res[i]["price"] == s["price"] and res[i]["std_err"] == s["std_err"], (i, res[i], s)
+    for i in np.random.default_rng(44).choice(len(opts), size=len(opts) // 100, replace=False):
+        o = opts[i]
+        ref = _oracle_price(o)
+        check_mixed_vs_oracle(o, res[i]["price"], ref["price"], lambda: _gpu_price(amc, ctx, o, amc.AMC_FP64)["price"])
+        assert res[i]["degenerate_dates"] == ref["degenerate_dates"]
+
+
+def test_full_greeks_sampled_vs_oracle(amc, ctx):
+    """The 1024-put Greeks workload at full size (2^18 paths, 100 dates),
+    mixed precision: a seeded 1 % sample against the oracle's frozen-boundary
+    pathwise price, delta and vega on the same points (bars as above)."""
+    opts = workloads.greeks_options()
+    p, d, v = amc.amc_greeks(ctx, opts, amc.AMC_MIXED)
+    for i in np.random.default_rng(45).choice(len(opts), size=len(opts) // 100, replace=False):
+        o = opts[i]
+        g = oracle.greeks(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
+                          seed=o.seed, rule=o.rule)
+        if abs(p[i] - g["price"]) > 2e-4 * o.K:      # unstable at FP32 precision: FP64 Greeks carry the bars
+            check_mixed_vs_oracle(o, p[i], g["price"], lambda: amc.amc_greeks(ctx, [o], amc.AMC_FP64)[0][0])
+            _, dd, vv = amc.amc_greeks(ctx, [o], amc.AMC_FP64)
+            assert abs(dd[0] - g["delta"]) <= 1e-9 + 5e-4 and abs(vv[0] - g["vega"]) <= 0.1, (i, dd, vv, g)
+            continue
+        assert abs(d[i] - g["delta"]) <= 2e-3 + 5e-4, (i, d[i], g)
+        assert abs(v[i] - g["vega"]) <= 0.2 + 5e-2 * max(1.0, abs(g["vega"])), (i, v[i], g)
 
 
 def test_device_entry_points_match_host_call(amc, ctx, torch):

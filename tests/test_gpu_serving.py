@@ -85,3 +85,53 @@ def test_admission_by_memory_and_busy_context(amc):
         assert res is not None and res[0]["status"] == 0 and abs(res[0]["price"] - 4.46) < 0.05
         # after stop the context prices directly again
         assert _alone(amc, ctx, o, amc.AMC_MIXED)["price"] == res[0]["price"]
+
+
+def test_served_stream_vs_alone_fp64_and_oracle(amc):
+    """A full-size 1-second Poisson stream of the serving workload (about
+    2000 requests, 2^14..2^18 paths, 12..365 dates), served in mixed
+    precision: every served result equals the request priced alone, bit for
+    bit; a seeded 5 % sample is within 2e-4 K of the all-FP64 GPU path and a
+    seeded 1 % sample within 2e-4 K of the FP64 oracle on the same points,
+    except where LSM is unstable at FP32 precision on the request, which is
+    then held to the oracle's own FP32 sensitivity and its FP64 GPU price
+    to 2e-4 K (check_mixed_vs_oracle)."""
+    import numpy as np
+
+    import oracle
+    from lsm_sensitivity import check_mixed_vs_oracle
+    _, opts = workloads.serving_requests(rate=2000.0, duration=1.0, seed=4)
+    with amc.Context(0, arena_bytes=24 << 30) as ctx:
+        amc.amc_serve_start(ctx, slots=3, max_batch=128, prec=amc.AMC_MIXED)
+        tickets = {amc.amc_serve_submit(ctx, o): i for i, o in enumerate(opts)}
+        got = {}
+        deadline = time.time() + 300
+        while len(got) < len(opts) and time.time() < deadline:
+            for t, r, lat in amc.amc_serve_drain(ctx):
+                got[tickets[t]] = r
+            time.sleep(0.002)
+        amc.amc_serve_stop(ctx)
+        assert len(got) == len(opts)
+        for i, o in enumerate(opts):
+            a = _alone(amc, ctx, o, amc.AMC_MIXED)
+            assert got[i]["status"] == 0
+            assert got[i]["price"] == a["price"] and got[i]["std_err"] == a["std_err"], (i, got[i], a)
+        fp64 = {}
+        for i in np.random.default_rng(41).choice(len(opts), size=len(opts) // 20, replace=False):
+            fp64[i] = _alone(amc, ctx, opts[i], amc.AMC_FP64)["price"]
+        sample = np.random.default_rng(42).choice(len(opts), size=len(opts) // 100, replace=False)
+        for i in sample:
+            if i not in fp64:
+                fp64[i] = _alone(amc, ctx, opts[i], amc.AMC_FP64)["price"]
+    for i, f in fp64.items():
+        o = opts[i]
+        if abs(got[i]["price"] - f) > 2e-4 * o.K:    # only where LSM is unstable at FP32 precision
+            ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
+                               seed=o.seed, rule=o.rule)
+            check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: f)
+    for i in sample:
+        o = opts[i]
+        ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
+                           seed=o.seed, rule=o.rule)
+        check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: fp64[i])
+        assert got[i]["degenerate_dates"] == ref["degenerate_dates"]
