@@ -248,6 +248,17 @@ def oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warmup=3):
     nbytes = 4.0 * units
     gbs = nbytes / (ms * 1e-3) / 1e9
     val = amc.res_to_dict(res.cpu().numpy())
+    # the same valuation with no path array: generation and valuation in one kernel
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            amc.amc_price_fused(ctx, vopt, amc.AMC_MIXED, res, coef, stream=stream)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            amc.amc_price_fused(ctx, vopt, amc.AMC_MIXED, res, coef, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    fused_ms = e0.elapsed_time(e1) / reps
     amc.amc_price_oos(ctx, opt, opt.seed + 5, amc.AMC_MIXED)
     t = time.perf_counter()
     fit, val2 = amc.amc_price_oos(ctx, opt, opt.seed + 5, amc.AMC_MIXED)
@@ -258,7 +269,7 @@ def oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warmup=3):
                                                     "profiles/value_boundary_2p20x252_mixed.md"),
                          "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
             "price_out_of_sample": val2["price"], "std_err": val2["std_err"], "price_in_sample": fit["price"],
-            "oos_pricing_ms": host_ms,
+            "oos_pricing_ms": host_ms, "fused_generate_and_value_ms": fused_ms,
             "workload": "boundary fitted on shift seed 2, applied to the 2^20 x 252 paths of shift seed 7"}
 
 
@@ -285,7 +296,8 @@ def paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warm
     nbytes = 4.0 * opt.n_paths * (opt.n_steps - 1)
     gbs = nbytes / (ms * 1e-3) / 1e9
     got = amc.res_to_dict(res.cpu().numpy())
-    return {"kernel": "sweep_pathwise_kernel (paper rule)", "ms": ms,
+    fused = fused_bench(amc, ctx, torch, stream, popt, reps, warmup)
+    return {"fused": fused, "kernel": "sweep_pathwise_kernel (paper rule)", "ms": ms,
             "value": opt.n_paths * opt.n_steps / (ms * 1e-3), "unit": METRIC,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "traffic": profile_traffic("paper_1205_0106_gb300/csrc/sweep.cu",
@@ -357,6 +369,40 @@ def dual_bench(amc, ctx, torch, stream, opt, reps=5, warmup=2):
             "lower": lo["price"], "lower_std_err": lo["std_err"], "gap": float(r[0]) - lo["price"],
             "workload": "boundary fitted on the 2^20 x 252 paths of shift seed 2; 4096 outer paths of shift "
                         "seed 13, 128 inner paths per outer path and date, inner seed 13"}
+
+
+def fused_bench(amc, ctx, torch, stream, popt, reps, warmup):
+    """The paper's rule priced with no path array (amc_price_fused: one
+    path-generation kernel that values every path as it is formed, then
+    finalize), timed with CUDA events on its stream; the stored-path
+    pricing (path generation + the rule's sweep) beside it."""
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+    ld = amc.amc_path_ld(popt.n_paths)
+    S = torch.empty((popt.n_steps, ld), dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: amc.amc_price_fused(ctx, popt, amc.AMC_MIXED, res, stream=stream))
+    fused_price = amc.res_to_dict(res.cpu().numpy())["price"]
+    ms_stored = timed(lambda: amc.amc_price_device(ctx, popt, amc.AMC_MIXED, S, res, stream=stream))
+    units = popt.n_paths * popt.n_steps
+    summary = "profiles/pathgen_fused_paper_2p20x252_mixed.md"
+    rl = issue_roofline("paper_1205_0106_gb300/csrc/pathgen.cu", summary, units / (ms * 1e-3))
+    rl["traffic"] = profile_traffic("paper_1205_0106_gb300/csrc/pathgen.cu", summary)
+    return {"ms": ms, "value": units / (ms * 1e-3), "unit": METRIC, "price": fused_price, "roofline": rl,
+            "stored_ms": ms_stored, "stored_over_fused": ms_stored / ms,
+            "workload": "Eqs. 10-11 on the 2^20 x 252 points of shift seed 2, no path array"}
 
 
 def fig1_bench(amc, device):
@@ -581,6 +627,20 @@ def run_amc(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    if args.profile_fused:
+        # profiling mode: only the paper rule priced with no path array (for ncu)
+        popt = workloads.Option(**{**opt.as_dict(), "rule": workloads.RULE_PAPER_UB})
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup + args.steps):
+                amc.amc_price_fused(ctx, popt, amc.AMC_MIXED, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "fused", "steps": args.steps, "warmup": args.warmup}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile_dual:
         # profiling mode: fit once, outer paths, then only the dual launches (for ncu)
         So, coef, outer = dual_setup(amc, ctx, torch, stream, opt)
@@ -715,6 +775,8 @@ def main():
                     help="run only the paper-rule sweeps (for ncu captures)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only the 4096-option batch, twice (for ncu launch lists)")
+    ap.add_argument("--profile-fused", action="store_true",
+                    help="run only the paper rule priced with no path array (for ncu captures)")
     ap.add_argument("--profile-dual", action="store_true",
                     help="fit the boundary, then run only two dual upper-bound launches (for ncu captures)")
     ap.add_argument("--profile", action="store_true", help="run only the timed mixed steps (for ncu captures)")
@@ -722,7 +784,7 @@ def main():
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper or args.profile_batch
-                                or args.profile_dual):
+                                or args.profile_dual or args.profile_fused):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

@@ -195,6 +195,22 @@ int amc_fit_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *
 int amc_value_boundary(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
                        int64_t ld, const double *coef_dev, double *res_dev, void *stream);
 
+/* Steps 1-4 with no path array: path generation values every path as its
+ * dates are formed (the bridge forms them out of order) and stores nothing,
+ * for the rules that need no regression across paths.  AMC_RULE_PAPER_UB:
+ * Eqs. 10-11, whose backward recursion is the maximum over t_0..t_{m-1} of
+ * the discounted payoffs, with the Black-Scholes value over the last
+ * interval taken at t_{m-1}; AMC_RULE_EUROPEAN: Eqs. 6-8; AMC_RULE_LSM with
+ * a fitted boundary coef_dev (as written by amc_fit_boundary): the
+ * valuation of amc_value_boundary on the option's own points (paths of
+ * opt->seed), which is the out-of-sample price when the boundary was fitted
+ * on other points.  coef_dev must be null for the other rules.  Result
+ * block as amc_sweep / amc_value_boundary.  Same points and decisions as
+ * generating, storing and then sweeping the paths; the sums are taken in
+ * another fixed order.  Asynchronous.                                      */
+int amc_price_fused(amc_ctx *ctx, const amc_option *opt, int prec, const double *coef_dev, double *res_dev,
+                    void *stream);
+
 /* Dual upper bound of a fitted boundary (the dual formulation of §IV,
  * ref. [11], with the Andersen-Broadie martingale of the boundary).  On each
  * outer path i of S (an AMC_RULE_LSM option's paths, as amc_sweep) and for

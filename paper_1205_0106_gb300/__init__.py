@@ -92,6 +92,7 @@ SIGNATURES = {
     "amc_fit_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_value_boundary": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "amc_price_oos": (ctypes.c_int, [_vp, _optp, _u64, ctypes.c_int, _resp, _resp]),
+    "amc_price_fused": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _vp, _vp]),
     "amc_dual_upper": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp, _i64, _u64, _vp, _vp, _vp]),
     "amc_price_dual": (ctypes.c_int, [_vp, _optp, _u64, _i64, _i64, _u64, ctypes.c_int, _resp, _resp, _resp]),
     "amc_price_american": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -322,6 +323,13 @@ def amc_price_oos(ctx, opt, value_seed, prec=AMC_MIXED):
     _check(lib().amc_price_oos(ctx.handle, ctypes.byref(make_option(opt)), value_seed, prec, ctypes.byref(fit),
                                ctypes.byref(val)), "amc_price_oos")
     return _res_dict(fit), _res_dict(val)
+
+
+def amc_price_fused(ctx, opt, prec, res, coef=None, stream=None):
+    """Steps 1-4 without a path array: the paper's rule or the European
+    estimator, or (LSM) the valuation of the boundary coef on opt's points."""
+    _check(lib().amc_price_fused(ctx.handle, ctypes.byref(make_option(opt)), prec, _ptr(coef), _ptr(res),
+                                 _stream(stream)), "amc_price_fused")
 
 
 def amc_dual_upper(ctx, opt, prec, S, coef, n_inner, inner_seed, res, U=None, ld=None, stream=None):

@@ -1,4 +1,4 @@
-// Device helpers shared by the sweep kernels.
+// Device helpers shared by the sweep, valuation and path-generation kernels.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -84,6 +84,19 @@ template <typename Real>
 __device__ __forceinline__ Real payoff(bool put, Real s, Real K) {
     const Real h = put ? K - s : s - K;
     return h > Real(0) ? h : Real(0);
+}
+
+__device__ __forceinline__ float ncdf(float x) { return normcdff(x); }
+__device__ __forceinline__ double ncdf(double x) { return normcdf(x); }
+
+// Black-Scholes value over time tau, Eqs. 1-5 (put through Eq. 5: N(-d2), N(-d1)).
+template <typename Real>
+__device__ __forceinline__ Real bs_value(bool put, Real S, Real K, Real r, Real sig, Real tau) {
+    const Real sq = sig * sqrt(tau);
+    const Real d1 = (log(S / K) + (r + Real(0.5) * sig * sig) * tau) / sq;
+    const Real d2 = d1 - sq;
+    const Real dfk = K * exp(-r * tau);
+    return put ? dfk * ncdf(-d2) - S * ncdf(-d1) : S * ncdf(d1) - dfk * ncdf(d2);
 }
 
 }  // namespace dev

@@ -129,6 +129,13 @@ struct KArgs {
 cudaError_t launch_sobol(const uint32_t *V, int n_dims, int64_t n_points, const uint32_t *shift,
                          uint32_t *x, int64_t ld, cudaStream_t st);
 cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t st);
+// Path generation that values each path as it is formed and stores nothing
+// (pathgen.cu): the rules that need no regression across paths, and the
+// valuation of a fitted boundary.  One option (a.one); per-CTA sums into
+// a.one.fin[grid][4] for launch_finalize.
+enum { kStore = 0, kPaperRule = 1, kEuropean = 2, kBoundary = 3 };
+cudaError_t pathgen_fused_grid(const KArgs &a, int mode, bool fp64, int sm_count, int64_t *grid);
+cudaError_t launch_pathgen_fused(const KArgs &a, int mode, bool fp64, int64_t grid, cudaStream_t st);
 cudaError_t launch_sweep_lsm(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
                              cudaStream_t st);
 cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,

@@ -51,12 +51,17 @@ struct PG<true> {
 };
 
 // Shared-memory layout of the path-generation kernel: every sub-buffer
-// starts on a 32-byte boundary (uint4 and R4<double> accesses).
+// starts on a 32-byte boundary (uint4 and R4<double> accesses).  A kernel
+// that values a fitted boundary on the fly also holds the boundary (four
+// coefficients and a flag per date); one that takes the paper's rule holds
+// two discounted-payoff constants per date.
 struct PathgenSmem {
-    unsigned nodes, v, xb, W, total;
+    unsigned nodes, v, xb, W, coef, deg, total;
 };
 __host__ __device__ __forceinline__ unsigned al32(unsigned v) { return (v + 31u) & ~31u; }
-__host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int nslots, bool fp64) {
+__host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int nslots, bool fp64, int mode = 0) {
+    const bool boundary = mode == 3;
+    const unsigned per_date = boundary ? 4u : (mode == 1 ? 2u : 0u);
     PathgenSmem L;
     const unsigned node = fp64 ? (unsigned)sizeof(NodeD) : (unsigned)sizeof(NodeF);
     const unsigned real = fp64 ? 8u : 4u;
@@ -64,7 +69,9 @@ __host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int ns
     L.v = al32(L.nodes + node * (unsigned)max_m);
     L.xb = al32(L.v + 48u * (unsigned)max_m);
     L.W = al32(L.xb + 4u * (unsigned)max_m);
-    L.total = L.W + real * 4u * kPathgenThreads * (unsigned)nslots;
+    L.coef = al32(L.W + real * 4u * kPathgenThreads * (unsigned)nslots);
+    L.deg = al32(L.coef + real * per_date * (unsigned)max_m);
+    L.total = L.deg + (boundary ? (unsigned)max_m : 0u);
     return L;
 }
 
@@ -143,13 +150,32 @@ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 constexpr int kGB = ilog2(kTilePoints) - 1;       // Gray bits 1..kGB of the thread's point offset 4t
 static_assert((1 << ilog2(kTilePoints)) == kTilePoints && kGB + 1 < 12, "tile of 2^k points, direction numbers v_1..v_12");
 
-template <bool FP64>
+// MODE kStore writes the path array (steps 1-3).  The other modes value
+// every path as its dates are formed and store nothing; they need no
+// regression across paths, and their per-path value does not depend on the
+// order in which the bridge forms the dates:
+//   kPaperRule  Eqs. 10-11: the backward recursion V = max(h_j, e^{-r dt} V)
+//               from V_{m-1} = max(h_{m-1}, BS over [t_{m-1}, t_m]) down to
+//               t_0 (S_0 = S0) equals max_j e^{-r t_j} h_j, with the
+//               Black-Scholes term taken at t_{m-1}; a running maximum;
+//   kEuropean   Eqs. 6-8: e^{-rT} h(S_m);
+//   kBoundary   a fitted boundary (continuation value over K, polynomial in
+//               y = S/K - 1): the first date tau < m where it exercises (not
+//               flagged, in the money, h > c(y), in the valuation kernel's
+//               arithmetic), else tau = m; the value at t_1 is
+//               e^{-r (t_tau - t_1)} h(S_tau) (finalize adds the last e^{-r dt}).
+// Each CTA adds its paths' values and squares in FP64 into its own slot of
+// J.fin, in a fixed order, for finalize_kernel.
+template <bool FP64, int MODE>
 __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_constant__ KArgs a) {
     using Real = typename PG<FP64>::Real;
     using Node = typename PG<FP64>::Node;
     extern __shared__ __align__(32) unsigned char smem[];
     const int max_m = a.max_m;
-    const PathgenSmem L = pathgen_layout(max_m, a.max_slots, FP64);
+    const PathgenSmem L = pathgen_layout(max_m, a.max_slots, FP64, MODE);
+    Real(*s_c)[4] = reinterpret_cast<Real(*)[4]>(smem + L.coef);             // [m][4] boundary (units of K)
+    Real(*s_ab)[2] = reinterpret_cast<Real(*)[2]>(smem + L.coef);            // [m][2] paper rule: a_d, b_d
+    unsigned char *s_deg = smem + L.deg;                                    // [m] no exercise at the date
     Node *s_nodes = reinterpret_cast<Node *>(smem + L.nodes);
     uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][3]: v_1..v_12 of each dim
     uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift
@@ -164,6 +190,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     for (int b = 0; b < kGB; ++b) gm[b] = 0u - ((g4 >> (b + 1)) & 1u);
     int cur = -1;
     int m = 0, nslots = 0;
+    double vs1 = 0.0, vs2 = 0.0;                                          // this thread's path values (fused modes)
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
         const int jb = a.jobs ? find_job_by_tile(a.jobs, a.n_jobs, tile) : 0;
         const Job &J = a.jobs ? a.jobs[jb] : a.one;
@@ -177,6 +204,23 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             for (int i = tid; i < m; i += kPathgenThreads) s_nodes[i] = gn[i];
             for (int i = tid; i < 3 * m; i += kPathgenThreads)
                 s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 3) * 32) + (i % 3));
+            if (MODE == kPaperRule) {
+                // e^{-r t_d} h(S) = a_d + b_d S where h > 0 (put: a_d = e^{-r t_d} K, b_d = -e^{-r t_d})
+                for (int d = tid; d < m; d += kPathgenThreads) {
+                    const double df = exp(-J.r * J.dt * (double)(d + 1));
+                    const bool put = J.type == AMC_PUT;
+                    s_ab[d][0] = (Real)(put ? df * J.K : -df * J.K);
+                    s_ab[d][1] = (Real)(put ? -df : df);
+                }
+            }
+            if (MODE == kBoundary) {
+                for (int d = tid; d < m; d += kPathgenThreads) {
+                    const double *c = J.coef + (size_t)d * kCoefStride;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s_c[d][k] = k < J.p ? (Real)c[k] : Real(0);
+                    s_deg[d] = (d == m - 1 || c[4] != 0.0) ? 1 : 0;
+                }
+            }
             cur = jb;
         }
         for (int k = tid; k < m; k += kPathgenThreads) s_xb[k] = sobol_direct(V, k, base) ^ shift[k];
@@ -197,6 +241,28 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         // exponent per node: FP32 in base 2 (ex2), FP64 in base e
         const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
         const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
+        // fused modes: per-path state of the thread's 4 paths
+        const bool put = J.type == AMC_PUT;
+        const Real K = (Real)J.K, invK = (Real)J.invK, rr = (Real)J.r, vol = (Real)J.sigma;
+        const Real rdt = (Real)(J.r * J.dt);
+        Real acc[4];                // kPaperRule: running max; kEuropean: value; kBoundary: h(S_tau) / K
+        int tau[4];                 // kBoundary: first exercise date (m: none)
+        Real hm[4];                 // kBoundary: h(S_m) / K
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            tau[q] = m;
+            hm[q] = Real(0);
+            acc[q] = Real(0);
+            if (MODE == kPaperRule) {
+                const Real h0 = dev::payoff(put, (Real)J.S0, K);
+                if (m == 1) {
+                    const Real c0 = dev::bs_value(put, (Real)J.S0, K, rr, vol, (Real)J.T);
+                    acc[q] = h0 > c0 ? h0 : c0;
+                } else {
+                    acc[q] = h0;
+                }
+            }
+        }
 
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
@@ -213,15 +279,101 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             R4<Real> Wo, So;
             node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
             s_W[nd.so * kPathgenThreads + tid] = Wo;
-            if (store) {
-                Real *dst = S + (int64_t)(nd.date - 1) * ld;
-                if (FP64) {                                               // two 16-byte stores
-                    reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
-                    reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
-                } else {
-                    *reinterpret_cast<float4 *>(dst) = make_float4((float)So.v[0], (float)So.v[1],
-                                                                   (float)So.v[2], (float)So.v[3]);
+            if (MODE == kStore) {
+                if (store) {
+                    Real *dst = S + (int64_t)(nd.date - 1) * ld;
+                    if (FP64) {                                           // two 16-byte stores
+                        reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
+                        reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
+                    } else {
+                        *reinterpret_cast<float4 *>(dst) = make_float4((float)So.v[0], (float)So.v[1],
+                                                                       (float)So.v[2], (float)So.v[3]);
+                    }
                 }
+            } else if (MODE == kPaperRule) {
+                // running maximum of a_d + b_d S_d: where the payoff is 0 that
+                // value is <= 0 <= h(S0), the maximum's first term, so it never wins
+                const int d = nd.date;
+                if (d < m - 1) {
+                    const Real ad = s_ab[d - 1][0], bd = s_ab[d - 1][1];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fmax(acc[q], fma(bd, So.v[q], ad));
+                } else if (d == m - 1) {
+                    const Real dfd = exp(-rdt * (Real)d);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const Real h = dev::payoff(put, So.v[q], K);
+                        const Real c = dev::bs_value(put, So.v[q], K, rr, vol, (Real)J.dt);
+                        acc[q] = fmax(acc[q], dfd * (h > c ? h : c));
+                    }
+                }
+            } else if (MODE == kEuropean) {
+                if (nd.date == m) {
+                    const Real dfT = exp(-rr * (Real)J.T);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = dfT * dev::payoff(put, So.v[q], K);
+                }
+            } else {                                                      // kBoundary
+                const int d = nd.date;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const Real y = fma(So.v[q], invK, Real(-1));
+                    const Real h = put ? -y : y;
+                    if (d == m) {
+                        hm[q] = h > Real(0) ? h : Real(0);
+                    } else if (d < tau[q] && !s_deg[d - 1]) {
+                        const Real cont = fma(fma(fma(s_c[d - 1][3], y, s_c[d - 1][2]), y, s_c[d - 1][1]), y,
+                                              s_c[d - 1][0]);
+                        if ((put ? y < Real(0) : y > Real(0)) && h > cont) {
+                            tau[q] = d;
+                            acc[q] = h;
+                        }
+                    }
+                }
+            }
+        }
+        if (MODE != kStore) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((int64_t)base + t4 + q >= J.N) continue;
+                Real v = acc[q];
+                if (MODE == kBoundary) v = (tau[q] < m ? acc[q] : hm[q]) * exp(-rdt * (Real)(tau[q] - 1));
+                vs1 += (double)v;
+                vs2 += (double)v * (double)v;
+            }
+        }
+    }
+    if (MODE != kStore) {
+        // fixed-order CTA sum into this CTA's slot of J.fin (finalize_kernel)
+        __shared__ double red[kPathgenThreads / 32][2];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            vs1 += __shfl_xor_sync(0xffffffffu, vs1, off);
+            vs2 += __shfl_xor_sync(0xffffffffu, vs2, off);
+        }
+        if ((tid & 31) == 0) {
+            red[tid >> 5][0] = vs1;
+            red[tid >> 5][1] = vs2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const Job &J = a.one;
+            double b1 = 0.0, b2 = 0.0;
+            for (int w = 0; w < kPathgenThreads / 32; ++w) {
+                b1 += red[w][0];
+                b2 += red[w][1];
+            }
+            const double sc = MODE == kBoundary ? J.K : 1.0;                // kBoundary sums in units of K
+            double *fin = reinterpret_cast<double *>(J.fin) + (int64_t)blockIdx.x * 4;
+            fin[0] = sc * b1;
+            fin[1] = sc * sc * b2;
+            fin[2] = 0.0;
+            fin[3] = 0.0;
+            if (blockIdx.x == 0) {
+                int nd = 0;
+                if (MODE == kBoundary)
+                    for (int d = 0; d < J.m - 1; ++d) nd += s_deg[d];
+                J.res[4] = (double)nd;
             }
         }
     }
@@ -344,19 +496,63 @@ cudaError_t launch_pathgen_permuted(const PermArgs &a, bool fp64, int sm_count, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t st) {
-    const int64_t total_tiles = a.total;
-    if (total_tiles <= 0) return cudaSuccess;
-    size_t smem = pathgen_smem_bytes(a.max_m, a.max_slots, fp64);
-    auto kern = fp64 ? pathgen_kernel<true> : pathgen_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+
+using PathgenFn = void (*)(KArgs);
+
+PathgenFn pathgen_fn(int mode, bool fp64) {
+    switch (mode) {
+        case kPaperRule: return fp64 ? pathgen_kernel<true, kPaperRule> : pathgen_kernel<false, kPaperRule>;
+        case kEuropean: return fp64 ? pathgen_kernel<true, kEuropean> : pathgen_kernel<false, kEuropean>;
+        case kBoundary: return fp64 ? pathgen_kernel<true, kBoundary> : pathgen_kernel<false, kBoundary>;
+        default: return fp64 ? pathgen_kernel<true, kStore> : pathgen_kernel<false, kStore>;
+    }
+}
+
+// Persistent grid: as many CTAs as fit on the SMs, at most one per tile.
+cudaError_t pathgen_setup(const KArgs &a, int mode, bool fp64, int sm_count, PathgenFn *kern, size_t *smem,
+                          int64_t *grid) {
+    *smem = pathgen_layout(a.max_m, a.max_slots, fp64, mode).total;
+    *kern = pathgen_fn(mode, fp64);
+    cudaError_t e = cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathgenThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *kern, kPathgenThreads, *smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * sm_count;
-    if (grid > total_tiles) grid = total_tiles;
+    *grid = (int64_t)per_sm * sm_count;
+    if (*grid > a.total) *grid = a.total;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
+    PathgenFn kern;
+    size_t smem;
+    int64_t grid;
+    cudaError_t e = pathgen_setup(a, kStore, fp64, sm_count, &kern, &smem, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, kPathgenThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t pathgen_fused_grid(const KArgs &a, int mode, bool fp64, int sm_count, int64_t *grid) {
+    PathgenFn kern;
+    size_t smem;
+    *grid = 0;
+    if (a.total <= 0) return cudaSuccess;
+    return pathgen_setup(a, mode, fp64, sm_count, &kern, &smem, grid);
+}
+
+cudaError_t launch_pathgen_fused(const KArgs &a, int mode, bool fp64, int64_t grid, cudaStream_t st) {
+    if (a.total <= 0 || grid <= 0 || a.jobs != nullptr || mode == kStore) return cudaErrorInvalidValue;
+    PathgenFn kern;
+    size_t smem;
+    int64_t g;
+    cudaError_t e = pathgen_setup(a, mode, fp64, 1, &kern, &smem, &g);
+    if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, kPathgenThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

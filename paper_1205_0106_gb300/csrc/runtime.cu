@@ -255,6 +255,51 @@ int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     return AMC_OK;
 }
 
+// Steps 1-4 without a path array: path generation values every path as it
+// is formed (the paper's rule, the European estimator, or a fitted
+// boundary's valuation), then the fixed-order finalize.
+int do_fused(amc_ctx *c, const amc_option *o, int prec, const double *coef, double *res, cudaStream_t st) {
+    AMC_TRY(host_validate(o));
+    AMC_TRY(check_prec(prec));
+    const bool lsm = o->rule == AMC_RULE_LSM;
+    if (!res || ((uintptr_t)res & 7u) != 0 || (lsm != (coef != nullptr)) || ((uintptr_t)coef & 7u) != 0)
+        return AMC_EINVAL;
+    DevBridge *b;
+    AMC_TRY(get_bridge(c, o->n_steps, &b));
+    KArgs &a = c->args;
+    memset(&a, 0, sizeof(KArgs));
+    Job &J = a.one;
+    fill_job_common(o, &J);
+    host_shifts(o->seed, o->n_steps, a.shift_one);
+    J.nodes = prec == AMC_FP64 ? (const void *)b->nd : (const void *)b->nf;
+    J.nslots = b->nslots;
+    J.n_tiles = (o->n_paths + kTilePoints - 1) / kTilePoints;
+    J.coef = const_cast<double *>(coef);
+    J.res = res;
+    J.status = c->status1;
+    a.n_jobs = 1;
+    a.max_m = o->n_steps;
+    a.max_slots = b->nslots;
+    a.total = J.n_tiles;
+    a.V = c->V;
+    const int mode = lsm ? kBoundary : (o->rule == AMC_RULE_PAPER_UB ? kPaperRule : kEuropean);
+    int64_t grid = 0;
+    AMC_TRY_CUDA(pathgen_fused_grid(a, mode, prec == AMC_FP64, c->sm_count, &grid));
+    if (grid > c->finv_ctas) {                        // grown on demand (synchronises the device once)
+        cudaFree(c->finv);
+        c->finv = nullptr;
+        c->finv_ctas = 0;
+        if (cudaMalloc(&c->finv, sizeof(double) * 4 * (size_t)grid) != cudaSuccess) return AMC_ENOMEM;
+        c->finv_ctas = grid;
+    }
+    J.fin = c->finv;
+    J.n_cta = (int)grid;
+    AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
+    AMC_TRY_CUDA(launch_pathgen_fused(a, mode, prec == AMC_FP64, grid, st));
+    AMC_TRY_CUDA(launch_finalize(a, st));
+    return AMC_OK;
+}
+
 int do_dual(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, const double *coef, int64_t n_in,
             uint64_t seed_in, double *res, double *U, cudaStream_t st) {
     AMC_TRY(host_validate(o));
@@ -794,6 +839,14 @@ int amc_price_oos(amc_ctx *c, const amc_option *opt, uint64_t value_seed, int pr
     else if ((int32_t)h[5] != 0) s1 = (int32_t)h[5];
     int s2 = result_from(h + AMC_RES_DOUBLES, value);
     return s1 != AMC_OK ? s1 : s2;
+}
+
+int amc_price_fused(amc_ctx *c, const amc_option *opt, int prec, const double *coef_dev, double *res_dev,
+                    void *stream) {
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || !opt) return AMC_EINVAL;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    return do_fused(c, opt, prec, coef_dev, res_dev, (cudaStream_t)stream);
 }
 
 int amc_dual_upper(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, const double *coef_dev,

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "devutil.cuh"
 #include "internal.h"
 
 namespace amc {
@@ -76,24 +77,8 @@ __device__ __forceinline__ void load4(const double *row, int64_t i, double *o) {
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
-template <typename Real>
-__device__ __forceinline__ Real payoff(bool put, Real s, Real K) {
-    const Real h = put ? K - s : s - K;
-    return h > Real(0) ? h : Real(0);
-}
-
-__device__ __forceinline__ float ncdf(float x) { return normcdff(x); }
-__device__ __forceinline__ double ncdf(double x) { return normcdf(x); }
-
-// Black-Scholes value over time tau, Eqs. 1-5.
-template <typename Real>
-__device__ __forceinline__ Real bs_value(bool put, Real S, Real K, Real r, Real sig, Real tau) {
-    const Real sq = sig * sqrt(tau);
-    const Real d1 = (log(S / K) + (r + Real(0.5) * sig * sig) * tau) / sq;
-    const Real d2 = d1 - sq;
-    const Real dfk = K * exp(-r * tau);
-    return put ? dfk * ncdf(-d2) - S * ncdf(-d1) : S * ncdf(d1) - dfk * ncdf(d2);
-}
+using dev::bs_value;
+using dev::payoff;
 
 __device__ __forceinline__ int find_job_by_cta(const Job *__restrict__ jobs, int n_jobs, int cta) {
     int lo = 0, hi = n_jobs - 1;

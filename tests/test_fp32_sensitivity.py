@@ -43,3 +43,30 @@ def test_deep_in_the_money_call_of_the_batch_is_unstable_at_fp32_precision():
     assert oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"] < oracle.european(S, o.type, o.K, o.r, o.T)["price"]
     assert path_noise_spread(o, reps=2) > 2e-4
     assert fp32_sum_shift(o) > 2e-4
+
+
+def test_sixteen_bit_log_moneyness_storage_error():
+    """Error study for storing the path array as log(S/K) in 16 bits: on the
+    Longstaff-Schwartz Table 1 put and the 252-date put (2^16 paths), the
+    oracle's price on the rounded paths moves by less than 1e-4 K in FP16
+    and in BF16 (round to nearest even), half the price bar."""
+    import numpy as np
+
+    import oracle
+
+    def rounded(S, K, kind):
+        x = np.log(S / K)
+        if kind == "fp16":
+            xq = x.astype(np.float16).astype(np.float64)
+        else:
+            u = x.astype(np.float32).view(np.uint32)
+            u = ((u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000))
+            xq = u.astype(np.uint32).view(np.float32).astype(np.float64)
+        return K * np.exp(xq)
+
+    for o in (STABLE, workloads.scaled(workloads.single_large(), n_paths=2 ** 16)):
+        S = oracle.paths(o.S0, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.seed)
+        ref = oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"]
+        for kind in ("fp16", "bf16"):
+            got = oracle.lsm(rounded(S, o.K, kind), o.type, o.K, o.r, o.T, o.basis)["price"]
+            assert abs(got - ref) < 1e-4 * o.K, (o, kind, got, ref)
