@@ -1,10 +1,15 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Bars (see DESIGN.md "Tolerances"):
+Bars:
   Sobol' integers                      bit-exact
-  paths, FP64 path                     rtol 1e-11
-  paths, mixed (FP32) path             rtol 2e-5 (FP32 inverse normal,
-                                       bridge and ex2; derivation in the design doc)
+  paths, FP64 path                     rtol 1e-11 (CUDA's normcdfinv and exp
+                                       within about 1 ulp, a few ulp per
+                                       bridge level)
+  paths, mixed (FP32) path             rtol 2e-5: the FP32 uniform (2^-24), the
+                                       fitted quantile (<= 2.9e-7), lg2.approx
+                                       (2^-22), the FP32 bridge over <= 10
+                                       levels and ex2.approx with exponent
+                                       rounding (~6e-7), <~ 1e-5 worst case
   prices (every rule, both precisions) |dP| <= 2e-4 K on identical points
   repeated runs, batch vs single       bit-identical
 """
