@@ -307,20 +307,29 @@ def paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind, reps=20, warm
 
 
 DUAL_OUTER, DUAL_INNER = 4096, 128
-DUAL_SMS, DUAL_SM_MHZ = 152, 2070.0          # GB300 SMs, maximum SM clock
+# SM count and maximum SM clock for the issue-slot peak: set from the device
+# properties and the nvidia-smi samples of the run (GB300 nominal until then)
+DEVICE = {"sms": 152, "sm_max_mhz": 2070.0, "source": "nominal GB300"}
+
+
+def _pipes(v):
+    return {k: float(x) for k, x in (kv.split("=") for kv in v.split(","))}
 
 
 def issue_roofline(kernel_src, summary, units_per_s):
     """Issue-slot roofline of a kernel: warp instructions per unit of work
     from its committed ncu capture (hash-checked) x the units per second
-    timed by CUDA events, against 152 SMs x 4 schedulers x 1 warp
-    instruction per clock at the maximum SM clock."""
+    timed by CUDA events, against SMs x 4 schedulers x 1 warp instruction
+    per clock at the maximum SM clock; with the capture's pipe utilisation
+    (instructions executed, % of each pipe's peak)."""
     per_unit = profile_traffic(kernel_src, summary, "warp_instr_per_unit", float)
-    peak = DUAL_SMS * 4 * DUAL_SM_MHZ * 1e6
+    peak = DEVICE["sms"] * 4 * DEVICE["sm_max_mhz"] * 1e6
     achieved = None if per_unit is None else per_unit * units_per_s
     return {"bound": "alu", "unit": "warp-instr/s", "achieved": achieved, "peak": peak,
             "frac": None if achieved is None else achieved / peak, "warp_instr_per_unit": per_unit,
-            "peak_kind": "issue slots at the maximum SM clock"}
+            "pipes_pct_of_peak": profile_traffic(kernel_src, summary, "pipes_pct", _pipes),
+            "peak_kind": "issue slots: %d SMs x 4 schedulers x 1 warp instruction per clock at %.0f MHz (%s)" % (
+                DEVICE["sms"], DEVICE["sm_max_mhz"], DEVICE["source"])}
 
 
 def dual_setup(amc, ctx, torch, stream, opt):
@@ -670,6 +679,9 @@ def run_amc(args):
     clocks.start()
     t_ms, _, _, res = time_steps(amc.AMC_MIXED, args.steps, args.warmup)
     ck = clocks.stop()
+    DEVICE.update(sms=torch.cuda.get_device_properties(local).multi_processor_count,
+                  sm_max_mhz=float(ck["sm_max_mhz"]) if ck else DEVICE["sm_max_mhz"],
+                  source="device properties, nvidia-smi maximum SM clock" if ck else "device properties")
     t_ms = max_over_ranks(dist, t_ms, "cuda")
     ms_per_step = t_ms / args.steps
     value = units * ws / (ms_per_step * 1e-3)
