@@ -305,6 +305,34 @@ def test_greeks_vs_central_differences(amc, ctx):
     assert abs(v[0] - fd_v) < 0.05 * abs(fd_v) + 0.2
 
 
+def test_autograd_gradients_are_the_adjoint_greeks(amc, ctx):
+    """american_price through torch.autograd: the price and the gradients in
+    S0 and sigma are the adjoint kernel's price, delta and vega bit for bit,
+    and the gradient agrees with central differences of GPU prices."""
+    import torch
+
+    from paper_1205_0106_gb300.autograd import american_price
+    opts = [workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 10, 2 ** 16, basis=3, seed=5),
+            workloads.Option(44.0, 40.0, 0.06, 0.4, 2.0, 25, 2 ** 15, basis=3, seed=6)]
+    for prec in (amc.AMC_FP64, amc.AMC_MIXED):
+        S0 = torch.tensor([o.S0 for o in opts], dtype=torch.float64, device="cuda", requires_grad=True)
+        sig = torch.tensor([o.sigma for o in opts], dtype=torch.float64, device="cuda", requires_grad=True)
+        p = american_price(ctx, S0, sig, K=40.0, r=0.06, T=[o.T for o in opts], n_steps=[o.n_steps for o in opts],
+                           n_paths=[o.n_paths for o in opts], basis=3, seed=[o.seed for o in opts], prec=prec)
+        assert p.device == S0.device
+        p.sum().backward()
+        ref_p, ref_d, ref_v = amc.amc_greeks(ctx, opts, prec)
+        assert np.array_equal(p.detach().cpu().numpy(), ref_p)
+        assert np.array_equal(S0.grad.cpu().numpy(), ref_d) and np.array_equal(sig.grad.cpu().numpy(), ref_v)
+    o = opts[0]
+    bS = 1e-3 * o.S0
+    f = lambda s: _gpu_price(amc, ctx, workloads.Option(**{**o.as_dict(), "S0": s}), amc.AMC_FP64)["price"]
+    fd = (f(o.S0 + bS) - f(o.S0 - bS)) / (2 * bS)
+    S0 = torch.tensor([o.S0], dtype=torch.float64, requires_grad=True)
+    american_price(ctx, S0, o.sigma, o.K, o.r, o.T, o.n_steps, o.n_paths, seed=o.seed, prec=amc.AMC_FP64).backward()
+    assert abs(S0.grad.item() - fd) < 0.02 * abs(fd) + 5e-3
+
+
 # ------------------------------------------------------------------ failures
 def test_device_wait_timeout_is_reported_and_context_survives(amc, ctx):
     opt = workloads.scaled(workloads.single_large(), n_paths=2 ** 18, n_steps=20)
