@@ -180,6 +180,7 @@ def cpu_baseline(opt, n_sample=None):
         oracle.set_threads(cores)
     out["value_1core"] = n1 * opt.n_steps / dt1
     out["sample_1core"] = "first %d paths, all %d dates, one thread, %.2f s" % (n1, opt.n_steps, dt1)
+    out["table2"] = table2_oracle()
     return out, (res["price"] if n_sample == opt.n_paths else None)
 
 
@@ -412,6 +413,52 @@ def fused_bench(amc, ctx, torch, stream, popt, reps, warmup):
     return {"ms": ms, "value": units / (ms * 1e-3), "unit": METRIC, "price": fused_price, "roofline": rl,
             "stored_ms": ms_stored, "stored_over_fused": ms_stored / ms,
             "workload": "Eqs. 10-11 on the 2^20 x 252 points of shift seed 2, no path array"}
+
+
+TABLE2_PATHS = (10, 100, 1000, 10000, 100000, 200000, 300000, 500000, 1000000)
+TABLE2_OPTION = dict(S0=36.0, K=40.0, r=0.06, sigma=0.2, T=1.0, n_steps=10, basis=3, type=0, seed=1)
+
+
+def table2_bench(amc, ctx, reps=20):
+    """The paper's Table 2 experiment (one pricing vs the number of paths, ten
+    exercise dates) on one GB300: host wall time of one blocking
+    amc_price_american call (median of reps, after two warm-up calls), for
+    the paper's rule (Eqs. 10-11) and for LSM.  The paper prints no option
+    parameters; this uses the Longstaff-Schwartz Table 1 put."""
+    o = TABLE2_OPTION
+    rows = []
+    for n in TABLE2_PATHS:
+        row = {"paths": n}
+        for name, rule in (("paper_rule_ms", amc.AMC_RULE_PAPER_UB), ("lsm_ms", amc.AMC_RULE_LSM)):
+            call = lambda: amc.amc_price_american(ctx, o["S0"], o["K"], o["r"], o["sigma"], o["T"], o["n_steps"], n,
+                                                  o["basis"], o["type"], o["seed"], rule, amc.AMC_MIXED)
+            call()
+            call()
+            ts = []
+            for _ in range(reps):
+                t = time.perf_counter()
+                call()
+                ts.append((time.perf_counter() - t) * 1e3)
+            row[name] = statistics.median(ts)
+        rows.append(row)
+    return {"rows": rows, "workload": "put S0 36 K 40 r 0.06 sigma 0.2 T 1, 10 dates, basis 3, mixed; host wall "
+                                      "time of one blocking call, median of %d" % reps}
+
+
+def table2_oracle():
+    """The oracle (paths + the paper's rule, all host cores) on the Table 2
+    path counts: seconds per pricing."""
+    import oracle
+    o = TABLE2_OPTION
+    oracle.price(o["S0"], o["K"], o["r"], o["sigma"], o["T"], o["n_steps"], 10, basis=o["basis"], type=o["type"],
+                 seed=o["seed"], rule=oracle.RULE_PAPER_UB)            # loads the library and its tables
+    out = []
+    for n in TABLE2_PATHS:
+        t = time.perf_counter()
+        oracle.price(o["S0"], o["K"], o["r"], o["sigma"], o["T"], o["n_steps"], n, basis=o["basis"], type=o["type"],
+                     seed=o["seed"], rule=oracle.RULE_PAPER_UB)
+        out.append({"paths": n, "paper_rule_ms": (time.perf_counter() - t) * 1e3})
+    return out
 
 
 def fig1_bench(amc, device):
@@ -760,6 +807,7 @@ def run_amc(args):
     if not args.no_batch:
         line.update(batch_and_greeks(amc, local))
         line["fig1"] = fig1_bench(amc, local)
+        line["table2"] = table2_bench(amc, ctx)
     if not args.no_cpu_baseline:
         # the oracle on the whole workload: the CPU baseline, and its price on the same points
         line["cpu_baseline"], ref_price = cpu_baseline(opt)
