@@ -158,6 +158,11 @@ int64_t value_ctas(int64_t n_paths);            // CTAs of the boundary valuatio
 
 size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 
+// Launch facts computed once (launch.cpp): raise a kernel's dynamic
+// shared-memory limit to at least `smem`; its co-resident CTAs per SM.
+cudaError_t ensure_smem(const void *f, size_t smem);
+cudaError_t ctas_per_sm(const void *f, int threads, size_t smem, int *out);
+
 // Dual upper bound of a fitted boundary (dual.cu): the option, its outer
 // paths S [m][ld], boundary coef, result block and status word in `one`.
 struct DualArgs {

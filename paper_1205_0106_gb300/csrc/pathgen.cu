@@ -484,10 +484,10 @@ cudaError_t launch_pathgen_permuted(const PermArgs &a, bool fp64, int sm_count, 
     if (a.total <= 0) return cudaSuccess;
     size_t smem = pathgen_smem_bytes(a.one.m, a.max_slots, fp64);
     auto kern = fp64 ? pathgen_perm_kernel<true> : pathgen_perm_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void *)kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathgenThreads, smem);
+    e = ctas_per_sm((const void *)kern, kPathgenThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * sm_count;
@@ -514,10 +514,10 @@ cudaError_t pathgen_setup(const KArgs &a, int mode, bool fp64, int sm_count, Pat
                           int64_t *grid) {
     *smem = pathgen_layout(a.max_m, a.max_slots, fp64, mode).total;
     *kern = pathgen_fn(mode, fp64);
-    cudaError_t e = cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    cudaError_t e = ensure_smem((const void *)*kern, *smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *kern, kPathgenThreads, *smem);
+    e = ctas_per_sm((const void *)*kern, kPathgenThreads, *smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     *grid = (int64_t)per_sm * sm_count;

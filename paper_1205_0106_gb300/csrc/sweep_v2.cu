@@ -689,7 +689,7 @@ cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cud
     const void *f = greeks ? (put ? (const void *)sweep_lsm_v2_kernel<true, true> : (const void *)sweep_lsm_v2_kernel<true, false>)
                            : (put ? (const void *)sweep_lsm_v2_kernel<false, true> : (const void *)sweep_lsm_v2_kernel<false, false>);
     const int smem = (int)sizeof(SmemV2);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem(f, (size_t)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     return cudaLaunchCooperativeKernel(f, dim3((unsigned)total_ctas), dim3(kT), args, (size_t)smem, st);

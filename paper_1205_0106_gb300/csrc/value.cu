@@ -242,7 +242,7 @@ cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStrea
                          : (put ? (const void *)value_boundary_kernel<false, true>
                                 : (const void *)value_boundary_kernel<false, false>);
     const int smem = fp64 ? (int)sizeof(VSmem<true>) : (int)sizeof(VSmem<false>);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem(f, (size_t)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
     return cudaLaunchKernel(f, dim3((unsigned)ctas), dim3(kValueThreads), args, (size_t)smem, st);
