@@ -601,11 +601,17 @@ static uint64_t orc_splitmix64_at(uint64_t seed, uint64_t n)
     return z ^ (z >> 31);
 }
 
+/* Normal of inner step s (1-based) of inner path k from date j of outer
+ * path i: the inner path owns H = ceil(m/2) consecutive SplitMix64 outputs,
+ * numbers ((i m + j - 1) n_in + k) H + 1 .. + H; steps 2q-1 and 2q take the
+ * high and the low 32 bits of its q-th output. */
 double orc_dual_normal(uint64_t seed_in, int m, int64_t n_in, int64_t i, int j, int64_t k, int s)
 {
-    uint64_t c = (((uint64_t)i * (uint64_t)m + (uint64_t)(j - 1)) * (uint64_t)n_in + (uint64_t)k) * (uint64_t)m
-                 + (uint64_t)(s - 1);
-    uint32_t x = (uint32_t)(orc_splitmix64_at(seed_in, c + 1) >> 32);
+    uint64_t H = ((uint64_t)m + 1u) / 2u;
+    uint64_t n = (((uint64_t)i * (uint64_t)m + (uint64_t)(j - 1)) * (uint64_t)n_in + (uint64_t)k) * H
+                 + (uint64_t)(s + 1) / 2u;
+    uint64_t out = orc_splitmix64_at(seed_in, n);
+    uint32_t x = (s & 1) ? (uint32_t)(out >> 32) : (uint32_t)out;
     return orc_norm_icdf(orc_uniform(x));
 }
 

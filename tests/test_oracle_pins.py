@@ -457,6 +457,9 @@ def test_permuted_points_give_an_unbiased_lsm_price():
 
 # ------------------------------------------------ dual upper bound (primal-dual)
 def test_dual_normals_are_counter_based_splitmix64():
+    """Inner path k from date j of outer path i owns ceil(m/2) consecutive
+    SplitMix64 outputs; steps 2q-1 and 2q take the high and low halves of
+    the q-th (recomputed here from SplitMix64's published constants)."""
     from scipy.special import ndtri
     M64 = (1 << 64) - 1
 
@@ -467,10 +470,13 @@ def test_dual_normals_are_counter_based_splitmix64():
         return z ^ (z >> 31)
 
     m, n_in = 7, 5
-    for (i, j, k, s) in [(0, 1, 0, 1), (3, 2, 4, 5), (11, 6, 2, 1)]:
-        c = ((i * m + j - 1) * n_in + k) * m + s - 1
-        x = sm64_at(9, c + 1) >> 32
+    H = (m + 1) // 2
+    for (i, j, k, s) in [(0, 1, 0, 1), (0, 1, 0, 2), (3, 2, 4, 5), (3, 2, 4, 6), (11, 6, 2, 1)]:
+        out = sm64_at(9, ((i * m + j - 1) * n_in + k) * H + (s + 1) // 2)
+        x = out >> 32 if s % 2 else out & 0xFFFFFFFF
         assert oracle.dual_normal(9, m, n_in, i, j, k, s) == pytest.approx(ndtri((x + 0.5) / 2.0 ** 32), rel=1e-13)
+    # consecutive inner paths own disjoint outputs: the last step of path k and the first of path k+1 differ
+    assert oracle.dual_normal(9, m, n_in, 0, 1, 0, m - 1) != oracle.dual_normal(9, m, n_in, 0, 1, 1, 1)
 
 
 def test_dual_with_one_date_is_the_european_estimator():
