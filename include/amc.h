@@ -223,12 +223,13 @@ int amc_price_fused(amc_ctx *ctx, const amc_option *opt, int prec, const double 
  * M_j = sum_{l<=j} (L_l - D_{l-1} Q_{l-1}) with D_0 Q_0 = L0:
  * U(i) = max_{j=1..m} (Z_j - M_j).  res_dev = [mean U, std_err of U, 0, 0,
  * flagged dates, status, L0, inner steps simulated]; U_dev[n_paths]
- * (device, 8-byte aligned,
- * may be null) receives U(i).  The inner normal of step s (1-based, to date
- * j + s) of inner path k (0-based) from date j of outer path i (0-based) is
- * Phi^-1((x + 1/2) 2^-32), x the high 32 bits of SplitMix64 output number
- * n = ((i m + j - 1) n_inner + k) m + s of inner_seed, that is
- * mix(inner_seed + n 0x9E3779B97F4A7C15).  FP32 inner paths under
+ * (device, 8-byte aligned, may be null) receives U(i).  Inner path k
+ * (0-based) from date j of outer path i (0-based) owns the H = ceil(m/2)
+ * SplitMix64 outputs number
+ * n = ((i m + j - 1) n_inner + k) H + q, q = 1..H, of inner_seed, that is
+ * mix(inner_seed + n 0x9E3779B97F4A7C15); its steps 2q-1 and 2q (to dates
+ * j + 2q - 1, j + 2q) take the normals Phi^-1((x + 1/2) 2^-32) of the high
+ * and of the low 32 bits x of output q.  FP32 inner paths under
  * AMC_MIXED (FP64 sums), all FP64 under AMC_FP64.  AMC_EINVAL for a rule
  * other than AMC_RULE_LSM, n_inner < 1 or > AMC_DUAL_MAX_INNER,
  * n_paths > 2^31 - 1, misaligned pointers, or more than AMC_DUAL_MAX_WORK

@@ -11,10 +11,12 @@
 // mean of L_1 over the outer paths) gives U(i) = max_j (Z_j - M_j), whose
 // mean is an upper bound on the Bermudan value.
 //
-// Inner normals come from a counter-based generator: step s of inner path k
-// started at date j on outer path i takes the high 32 bits of the
-// SplitMix64 output number ((i m + j - 1) n_in + k) m + s of inner_seed as
-// a uniform (x + 1/2) 2^-32, mapped by the inverse normal.
+// Inner normals come from a counter-based generator: inner path k started
+// at date j on outer path i owns the H = ceil(m/2) SplitMix64 outputs
+// ((i m + j - 1) n_in + k) H + 1 .. + H of inner_seed; steps 2q-1 and 2q
+// take the high and the low 32 bits of the q-th as uniforms (x + 1/2) 2^-32,
+// mapped by the inverse normal.  A loop trip draws one output and takes up
+// to two steps, so every lane calls the generator on every trip.
 //
 // dual_inner_kernel: one CTA per outer path.  Warps take dates in snake
 // order (most work first) and run their inner paths as a queue shared
@@ -38,11 +40,11 @@ namespace {
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;   // SplitMix64 increment
 
-// High 32 bits of the SplitMix64 output for the state z (already advanced).
-__device__ __forceinline__ uint32_t splitmix_hi(uint64_t z) {
+// SplitMix64 output for the state z (already advanced).
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return (uint32_t)((z ^ (z >> 31)) >> 32);
+    return z ^ (z >> 31);
 }
 
 template <bool FP64>
@@ -71,17 +73,16 @@ __host__ __device__ constexpr size_t dual_smem_bytes(int m) {
 }
 
 // One step of an inner path: S (FP64) or log(S/K) (FP32) moves to date d by
-// the normal of the 32-bit uniform u; returns whether the path stops at d
-// (the boundary exercises, or d = m) and h(S_d) / K in hk.
+// the normal zn; returns whether the path stops at d (the boundary
+// exercises, or d = m) and h(S_d) / K in hk.
 template <bool FP64, bool PUT>
-__device__ __forceinline__ bool inner_step(typename DualReal<FP64>::T &x, uint32_t u, int d, int m,
+__device__ __forceinline__ bool inner_step(typename DualReal<FP64>::T &x, typename DualReal<FP64>::T zn, int d, int m,
                                            typename DualReal<FP64>::T drift, typename DualReal<FP64>::T vol,
                                            double K, typename DualReal<FP64>::T invK,
                                            const typename DualReal<FP64>::T *__restrict__ cf,
                                            const int32_t *__restrict__ deg, typename DualReal<FP64>::T &hk) {
     bool stop = d >= m;
     if constexpr (FP64) {
-        const double zn = normcdfinv(((double)u + 0.5) * 0x1p-32);
         x = x * exp(drift + vol * zn);
         hk = (PUT ? K - x : x - K) * invK;
         if (!stop && hk > 0.0 && !deg[d - 1]) {
@@ -90,7 +91,7 @@ __device__ __forceinline__ bool inner_step(typename DualReal<FP64>::T &x, uint32
             stop = hk > fma(fma(fma(c[3], y, c[2]), y, c[1]), y, c[0]);
         }
     } else {
-        x += fmaf(vol, icdf_u32(u), drift);        // log(S_d / K)
+        x += fmaf(vol, zn, drift);                  // log(S_d / K)
         const float sk = expf(x);
         hk = PUT ? 1.f - sk : sk - 1.f;
         if (!stop && hk > 0.f && !deg[d - 1]) {
@@ -141,12 +142,13 @@ __device__ __forceinline__ void warp_dates(const DualArgs &a, int64_t i, int lan
     const Real vol = (Real)(J.sigma * sqrt(J.dt));
     const Real rdt = (Real)(J.r * J.dt);
     const Real invK = (Real)J.invK;
-    const uint64_t mG = (uint64_t)m * kGolden;
-    // SplitMix64 state of step 1 of inner path k from date j:
-    // seed + (((i m + j - 1) n_in + k) m + 1) golden = z0(j) + k m golden
+    const uint64_t H = ((uint64_t)m + 1ull) / 2ull;                       // outputs per inner path
+    const uint64_t mG = H * kGolden;
+    // SplitMix64 state of the first output of inner path k from date j:
+    // seed + (((i m + j - 1) n_in + k) H + 1) golden = z0(j) + k H golden
     auto z0 = [&](int j) -> uint64_t {
         const uint64_t base = ((uint64_t)i * (uint64_t)m + (uint64_t)(j - 1)) * (uint64_t)n_in;
-        return a.seed_in + (base * (uint64_t)m + 1ull) * kGolden;
+        return a.seed_in + (base * H + 1ull) * kGolden;
     };
     int round = 0;
     int jA = snake_date(round++, warp, n_warps, m), jB = snake_date(round++, warp, n_warps, m);
@@ -158,11 +160,25 @@ __device__ __forceinline__ void warp_dates(const DualArgs &a, int64_t i, int lan
     uint64_t z = 0;
     for (;;) {
         if (active) {
-            ++s;
-            const uint32_t u = splitmix_hi(z);
+            // one generator output: the normals of the next two steps
+            const uint64_t out = splitmix_out(z);
             z += kGolden;
+            const uint32_t u1 = (uint32_t)(out >> 32), u2 = (uint32_t)out;
+            Real zn1, zn2;
+            if constexpr (FP64) {
+                zn1 = normcdfinv(((double)u1 + 0.5) * 0x1p-32);
+            } else {
+                icdf_u32x2(u1, u2, zn1, zn2);
+            }
             Real hk;
-            if (inner_step<FP64, PUT>(x, u, jl + s, m, drift, vol, J.K, invK, cf, deg, hk)) {
+            ++s;
+            bool stop = inner_step<FP64, PUT>(x, zn1, jl + s, m, drift, vol, J.K, invK, cf, deg, hk);
+            if (!stop) {
+                if constexpr (FP64) zn2 = normcdfinv(((double)u2 + 0.5) * 0x1p-32);
+                ++s;
+                stop = inner_step<FP64, PUT>(x, zn2, jl + s, m, drift, vol, J.K, invK, cf, deg, hk);
+            }
+            if (stop) {
                 Real v = (Real)0;
                 if (hk > (Real)0) {
                     if constexpr (FP64) v = hk * exp(-rdt * s);

@@ -86,10 +86,16 @@ __device__ __noinline__ float icdf_tail(uint32_t x, float y) {
 __device__ __forceinline__ float icdf_y(uint32_t x) {            // u - 1/2 from the signed offset
     return fmaf((float)(int32_t)(x ^ 0x80000000u), 0x1p-32f, 0x1p-33f);
 }
-// z = Phi^-1((x + 1/2) 2^-32): the central form, else the tail.
-__device__ __forceinline__ float icdf_u32(uint32_t x) {
-    const float y = icdf_y(x);
-    return fabsf(y) < 0.4983f ? icdf_central(y) : icdf_tail(x, y);
+// z = Phi^-1((x + 1/2) 2^-32) for two integers at once: the central form
+// in packed f32x2 arithmetic, then the tail for whichever lies outside it.
+__device__ __forceinline__ void icdf_u32x2(uint32_t x0, uint32_t x1, float &z0, float &z1) {
+    using namespace dev;
+    const f2 y = f2_pack(icdf_y(x0), icdf_y(x1));
+    const f2 zc = icdf_central2(y);
+    z0 = f2_lo(zc);
+    z1 = f2_hi(zc);
+    if (!(fabsf(f2_lo(y)) < 0.4983f)) z0 = icdf_tail(x0, f2_lo(y));
+    if (!(fabsf(f2_hi(y)) < 0.4983f)) z1 = icdf_tail(x1, f2_hi(y));
 }
 
 }  // namespace
