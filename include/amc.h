@@ -47,6 +47,7 @@ extern "C" {
 #define AMC_EBUSY (-5)    /* serving admission refused (memory or slots)    */
 #define AMC_PENDING (-6)  /* serving request not finished yet               */
 #define AMC_ENOTFOUND (-7)/* unknown serving ticket                         */
+#define AMC_ECANCELED (-8)/* serving request cancelled before it ran        */
 
 #define AMC_MAX_STEPS 512          /* direction-number table limit          */
 #define AMC_MAX_PATHS (1LL << 31)  /* 32-bit Sobol' point index             */
@@ -282,7 +283,7 @@ typedef struct amc_serve_config {
 } amc_serve_config;
 
 typedef struct amc_serve_stats {
-    int64_t submitted, launched, completed, rejected, batches, pending;
+    int64_t submitted, launched, completed, rejected, batches, pending, cancelled;
 } amc_serve_stats;
 
 /* Start the scheduler thread.  Admission is by memory footprint: a request
@@ -298,6 +299,11 @@ int amc_serve_poll(amc_ctx *ctx, uint64_t ticket, amc_result *out, double *laten
 /* Up to `cap` finished requests, released; *n_out of them.  Thread-safe.   */
 int amc_serve_drain(amc_ctx *ctx, uint64_t *tickets, amc_result *out, double *latency_s, int cap,
                     int *n_out);
+/* Cancel a request that is still queued: it leaves the queue and finishes
+ * at once with status AMC_ECANCELED (poll / drain hand it out).  AMC_EBUSY
+ * if it is already on the GPU or finished (it completes normally),
+ * AMC_ENOTFOUND for an unknown or released ticket.  Thread-safe.           */
+int amc_serve_cancel(amc_ctx *ctx, uint64_t ticket);
 int amc_serve_stats_get(amc_ctx *ctx, amc_serve_stats *out);
 /* Finish every queued request, then stop the scheduler.                    */
 int amc_serve_stop(amc_ctx *ctx);

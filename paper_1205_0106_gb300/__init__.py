@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libamc.so")
 
 AMC_OK, AMC_EINVAL, AMC_ENOMEM, AMC_ECUDA, AMC_ETIMEOUT, AMC_EBUSY, AMC_PENDING, AMC_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+AMC_ECANCELED = -8
 AMC_PUT, AMC_CALL = 0, 1
 AMC_RULE_LSM, AMC_RULE_PAPER_UB, AMC_RULE_EUROPEAN = 0, 1, 2
 AMC_FP64, AMC_MIXED = 0, 1
@@ -48,7 +49,8 @@ class amc_serve_config(ctypes.Structure):
 
 class amc_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("launched", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64), ("pending", ctypes.c_int64)]
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64)]
 
 
 class AmcError(RuntimeError):
@@ -105,6 +107,7 @@ SIGNATURES = {
     "amc_serve_poll": (ctypes.c_int, [_vp, _u64, _resp, _dp]),
     "amc_serve_drain": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _resp, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "amc_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(amc_serve_stats)]),
+    "amc_serve_cancel": (ctypes.c_int, [_vp, _u64]),
     "amc_serve_stop": (ctypes.c_int, [_vp]),
     "amc_sweep_noalloc": (ctypes.c_int, [_optp, ctypes.c_int, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "amc_sweep_noalloc_capacity": (ctypes.c_size_t, []),
@@ -383,6 +386,12 @@ def amc_serve_drain(ctx, cap=4096):
     n = ctypes.c_int()
     _check(lib().amc_serve_drain(ctx.handle, tk, rs, lat, cap, ctypes.byref(n)), "amc_serve_drain")
     return [(tk[i], _res_dict(rs[i]), lat[i]) for i in range(n.value)]
+
+
+def amc_serve_cancel(ctx, ticket):
+    """Cancel a queued request (it then finishes with status AMC_ECANCELED);
+    raises AmcError (AMC_EBUSY: already on the GPU or finished)."""
+    _check(lib().amc_serve_cancel(ctx.handle, ticket), "amc_serve_cancel")
 
 
 def amc_serve_stats_get(ctx):

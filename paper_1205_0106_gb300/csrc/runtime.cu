@@ -17,6 +17,7 @@
 using namespace amc;
 
 #include "ctx.h"
+#include "trace.h"
 
 namespace {
 
@@ -593,6 +594,7 @@ const char *amc_strerror(int code) {
         case AMC_EBUSY: return "admission refused";
         case AMC_PENDING: return "pending";
         case AMC_ENOTFOUND: return "unknown ticket";
+        case AMC_ECANCELED: return "request cancelled";
         default: return "unknown error";
     }
 }
@@ -757,6 +759,7 @@ int amc_sobol(amc_ctx *c, int n_dims, int64_t n_points, uint64_t seed, uint32_t 
 }
 
 int amc_generate_paths(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, int64_t ld, void *stream) {
+    TraceRange trace_range("amc_generate_paths");
     if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -779,6 +782,7 @@ int amc_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uin
 
 int amc_sweep(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, int with_greeks,
               double *res_dev, void *stream) {
+    TraceRange trace_range("amc_sweep");
     if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -787,6 +791,7 @@ int amc_sweep(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, in
 
 int amc_price_device(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, int64_t ld, double *res_dev,
                      void *stream) {
+    TraceRange trace_range("amc_price_device");
     if (c && c->server) return AMC_EBUSY;
     if (!c) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -796,6 +801,7 @@ int amc_price_device(amc_ctx *c, const amc_option *opt, int prec, void *S_dev, i
 
 int amc_fit_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, double *coef_dev,
                      double *res_dev, void *stream) {
+    TraceRange trace_range("amc_fit_boundary");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt || opt->rule != AMC_RULE_LSM || !coef_dev || ((uintptr_t)coef_dev & 7u) != 0) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -804,6 +810,7 @@ int amc_fit_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *S_
 
 int amc_value_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld,
                        const double *coef_dev, double *res_dev, void *stream) {
+    TraceRange trace_range("amc_value_boundary");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -812,6 +819,7 @@ int amc_value_boundary(amc_ctx *c, const amc_option *opt, int prec, const void *
 
 int amc_price_oos(amc_ctx *c, const amc_option *opt, uint64_t value_seed, int prec, amc_result *fit,
                   amc_result *value) {
+    TraceRange trace_range("amc_price_oos");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt || !value || opt->rule != AMC_RULE_LSM) return AMC_EINVAL;
     AMC_TRY(host_validate(opt));
@@ -843,6 +851,7 @@ int amc_price_oos(amc_ctx *c, const amc_option *opt, uint64_t value_seed, int pr
 
 int amc_price_fused(amc_ctx *c, const amc_option *opt, int prec, const double *coef_dev, double *res_dev,
                     void *stream) {
+    TraceRange trace_range("amc_price_fused");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -851,6 +860,7 @@ int amc_price_fused(amc_ctx *c, const amc_option *opt, int prec, const double *c
 
 int amc_dual_upper(amc_ctx *c, const amc_option *opt, int prec, const void *S_dev, int64_t ld, const double *coef_dev,
                    int64_t n_inner, uint64_t inner_seed, double *res_dev, double *U_dev, void *stream) {
+    TraceRange trace_range("amc_dual_upper");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -859,6 +869,7 @@ int amc_dual_upper(amc_ctx *c, const amc_option *opt, int prec, const void *S_de
 
 int amc_price_dual(amc_ctx *c, const amc_option *opt, uint64_t outer_seed, int64_t n_outer, int64_t n_inner,
                    uint64_t inner_seed, int prec, amc_result *fit, amc_result *lower, amc_result *upper) {
+    TraceRange trace_range("amc_price_dual");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !opt || !upper || opt->rule != AMC_RULE_LSM) return AMC_EINVAL;
     amc_option ov = *opt;
@@ -895,6 +906,7 @@ int amc_price_dual(amc_ctx *c, const amc_option *opt, uint64_t outer_seed, int64
 
 int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, double T, int n_steps,
                        int64_t n_paths, int basis, int type, uint64_t seed, int rule, int prec, amc_result *out) {
+    TraceRange trace_range("amc_price_american");
     if (c && c->server) return AMC_EBUSY;
     if (!c || !out) return AMC_EINVAL;
     amc_option o = make_option(S0, K, r, sigma, T, n_steps, n_paths, basis, type, seed, rule);
@@ -920,6 +932,7 @@ int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, 
 }
 
 int amc_price_batch(amc_ctx *c, const amc_option *opts, int n, int prec, amc_result *out) {
+    TraceRange trace_range("amc_price_batch");
     if (c && c->server) return AMC_EBUSY;
     if (!c || n < 0 || (n > 0 && (!opts || !out))) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
@@ -927,6 +940,7 @@ int amc_price_batch(amc_ctx *c, const amc_option *opts, int n, int prec, amc_res
 }
 
 int amc_greeks(amc_ctx *c, const amc_option *opts, int n, int prec, double *price, double *delta, double *vega) {
+    TraceRange trace_range("amc_greeks");
     if (c && c->server) return AMC_EBUSY;
     if (!c || n < 0 || (n > 0 && (!opts || !price || !delta || !vega))) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "trace.h"
 
 namespace amc {
 
@@ -82,6 +83,7 @@ struct Server {
 // around the launch.
 bool Server::launch_into(Slot &sl, std::unique_lock<std::mutex> &lk) {
     if (pending.empty()) return false;
+    TraceRange trace_range("amc serve batch");
     const Request &head = reqs[pending.front()];
     const GroupKey key = head.key;
     const int cap = group_cta_cap(c, head.plan);
@@ -288,6 +290,26 @@ int amc_serve_drain(amc_ctx *c, uint64_t *tickets, amc_result *out, double *late
         }
     }
     *n_out = n;
+    return AMC_OK;
+}
+
+int amc_serve_cancel(amc_ctx *c, uint64_t ticket) {
+    if (!c) return AMC_EINVAL;
+    Server *s = c->server;
+    if (!s) return AMC_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return AMC_ENOTFOUND;
+    auto q = std::find(s->pending.begin(), s->pending.end(), ticket);
+    if (q == s->pending.end()) return AMC_EBUSY;   // in a batch on the GPU, or finished
+    s->pending.erase(q);
+    Request &r = it->second;
+    memset(&r.res, 0, sizeof(r.res));
+    r.res.status = AMC_ECANCELED;
+    r.done = true;
+    r.t_done = now_s();
+    s->stats.cancelled += 1;
+    s->cv.notify_all();
     return AMC_OK;
 }
 

@@ -38,6 +38,7 @@ def test_exports_every_declared_function(amc):
 def test_strerror_and_version(amc):
     assert amc.strerror(0) == "ok"
     assert "timed out" in amc.strerror(amc.AMC_ETIMEOUT)
+    assert "cancel" in amc.strerror(amc.AMC_ECANCELED)
     assert amc.amc_version() >= 1
 
 

@@ -135,3 +135,40 @@ def test_served_stream_vs_alone_fp64_and_oracle(amc):
                            seed=o.seed, rule=o.rule)
         check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: fp64[i])
         assert got[i]["degenerate_dates"] == ref["degenerate_dates"]
+
+
+def test_cancel_a_queued_request(amc):
+    """One slot busy with a large request: a request queued behind it can be
+    cancelled (it finishes at once with AMC_ECANCELED and never runs); the
+    running one cannot (AMC_EBUSY) and completes with its normal result;
+    an unknown ticket gives AMC_ENOTFOUND; the other queued requests still
+    run and equal their results alone."""
+    big = workloads.single_large()
+    small = [workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 50, 2 ** 14, basis=3, seed=40 + k) for k in range(3)]
+    with amc.Context(0, arena_bytes=4 << 30) as ctx:
+        alone = [_alone(amc, ctx, o, amc.AMC_MIXED) for o in small + [big]]
+        amc.amc_serve_start(ctx, slots=1, max_batch=8, prec=amc.AMC_MIXED)
+        t_big = amc.amc_serve_submit(ctx, big)
+        deadline = time.time() + 30
+        while amc.amc_serve_stats_get(ctx)["launched"] < 1 and time.time() < deadline:
+            time.sleep(0.0002)
+        tickets = [amc.amc_serve_submit(ctx, o) for o in small]
+        amc.amc_serve_cancel(ctx, tickets[1])
+        with pytest.raises(amc.AmcError) as ei:
+            amc.amc_serve_cancel(ctx, t_big)
+        assert ei.value.code == amc.AMC_EBUSY
+        with pytest.raises(amc.AmcError) as ei:
+            amc.amc_serve_cancel(ctx, 987654321)
+        assert ei.value.code == amc.AMC_ENOTFOUND
+        got = {}
+        while len(got) < 4 and time.time() < deadline:
+            for t, r, lat in amc.amc_serve_drain(ctx):
+                got[t] = r
+            time.sleep(0.002)
+        stats = amc.amc_serve_stats_get(ctx)
+        amc.amc_serve_stop(ctx)
+    assert got[tickets[1]]["status"] == amc.AMC_ECANCELED
+    assert stats["cancelled"] == 1 and stats["launched"] == 3
+    for k in (0, 2):
+        assert got[tickets[k]]["status"] == 0 and got[tickets[k]]["price"] == alone[k]["price"]
+    assert got[t_big]["status"] == 0 and got[t_big]["price"] == alone[3]["price"]
