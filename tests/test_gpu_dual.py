@@ -82,12 +82,23 @@ DUAL_CASES = [
     ("deep_otm_degenerate", workloads.Option(200.0, 40.0, 0.06, 0.2, 1.0, 20, 300, basis=3, seed=34), 2000, 4, 32),
     ("one_date", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 4096, seed=35), 4096, 5, 8),
     ("many_warps_few_lanes", workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 40, 129, basis=3, seed=36), 8192, 6, 5),
+    ("max_dates", workloads.Option(100.0, 100.0, 0.05, 0.3, 2.0, 512, 40, basis=4, seed=37), 8192, 7, 4),
 ]
+
+
+# The 512-date case (the largest shared-memory layout) is held to the FP64
+# bars only: each outer path takes about 1e5 FP32 stopping decisions there,
+# so a few land within the FP32 error of the boundary, and with 4 inner paths
+# each such flip moves a continuation estimate by a quarter of a payoff; the
+# mean over 40 outer paths then moves by far more than 2e-4 K.
+FP64_ONLY = {"max_dates"}
 
 
 @pytest.mark.parametrize("name,opt,n_fit,fit_seed,n_in", DUAL_CASES, ids=[c[0] for c in DUAL_CASES])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_dual_with_the_oracle_boundary_vs_oracle(amc, ctx, torch, name, opt, n_fit, fit_seed, n_in, prec):
+    if prec == amc.AMC_MIXED and name in FP64_ONLY:
+        pytest.skip("FP32 inner decisions at 512 dates with 4 inner paths: FP64 bars only")
     beta, deg = _oracle_boundary(opt, n_fit, fit_seed)
     seed_in = 1000 + opt.seed
     res, U = _gpu_dual(amc, ctx, torch, opt, prec, _coef(amc, torch, opt, beta, deg), n_in, seed_in)

@@ -68,6 +68,7 @@ CASES = [
     ("ls_table1_european", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 50, 2 ** 14, seed=1, rule=EU)),
     ("ragged_call_european", workloads.Option(105.0, 100.0, 0.04, 0.25, 0.75, 7, 12345, type=1, seed=11, rule=EU)),
     ("one_date_european", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 5, seed=3, rule=EU)),
+    ("max_dates_paper", workloads.Option(100.0, 100.0, 0.05, 0.3, 2.0, 512, 3000, seed=16, rule=PW)),
 ]
 
 
@@ -100,6 +101,7 @@ BOUNDARY_CASES = [
     ("ragged_put_p4", workloads.Option(95.0, 100.0, 0.07, 0.35, 1.5, 100, 30001, basis=4, seed=12)),
     ("deep_otm_degenerate", workloads.Option(200.0, 40.0, 0.06, 0.2, 1.0, 20, 2000, basis=3, seed=18)),
     ("one_date", workloads.Option(36.0, 40.0, 0.06, 0.2, 1.0, 1, 4096, seed=13)),
+    ("max_dates", workloads.Option(100.0, 100.0, 0.05, 0.3, 2.0, 512, 3000, basis=4, seed=17)),
 ]
 
 
