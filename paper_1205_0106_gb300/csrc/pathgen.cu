@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
 
         // unrolled in the store mode: the quantile of later nodes overlaps the
         // bridge and store of earlier ones (0.442 -> 0.405 ms on 2^20 x 252)
-#pragma unroll (MODE == kStore ? 8 : 1)
+#pragma unroll ((MODE == kStore || (MODE == kPaperRule && !FP64)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
             const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];

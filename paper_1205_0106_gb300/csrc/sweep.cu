@@ -486,6 +486,7 @@ sweep_pathwise_kernel(const __grid_constant__ KArgs a) {
                 V[q] = h > c ? h : c;
             }
         }
+#pragma unroll 4
         for (int j = m - 2; j >= 1; --j) {
             const Real *row = S + (int64_t)(j - 1) * ld;
             Real s[P];
