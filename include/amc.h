@@ -57,7 +57,14 @@ enum { AMC_PUT = 0, AMC_CALL = 1 };
  * pathwise rule, Eqs. 10-11 (an upper bound, §V); European, Eqs. 6-8.      */
 enum { AMC_RULE_LSM = 0, AMC_RULE_PAPER_UB = 1, AMC_RULE_EUROPEAN = 2 };
 /* Precision: all-FP64 paths, sums and solve; or FP32 paths with
- * compensated (double-float) FP32 sums, FP64 solve and FP64 final price.   */
+ * compensated (double-float) FP32 sums, FP64 solve and FP64 final price.
+ * AMC_MIXED stays within 2e-4 K of the FP64 estimate where the LSM
+ * estimator is stable at FP32 precision.  Where a wide moneyness range
+ * meets a rich basis (volatility 150 % with p = 4, a 10-year call at 40 %
+ * with p = 4, a call with S0/K = 1.4, sigma 34 %, T = 1.7 and p = 3),
+ * exercise decisions near the fitted boundary flip under perturbations of
+ * order 1e-7 and the FP64 estimate itself moves by more than 2e-4 K under
+ * FP32-level noise; price such options with AMC_FP64 (or a smaller basis).  */
 enum { AMC_FP64 = 0, AMC_MIXED = 1 };
 
 /* One option.  72 bytes, naturally aligned.                                */
