@@ -243,7 +243,7 @@ int amc_price_fused(amc_ctx *ctx, const amc_option *opt, int prec, const double 
  * n_paths > 2^31 - 1, misaligned pointers, or more than AMC_DUAL_MAX_WORK
  * possible inner steps (n_paths n_inner m (m-1) / 2).  Asynchronous.      */
 #define AMC_DUAL_MAX_WORK (1LL << 40)
-#define AMC_DUAL_MAX_INNER (1LL << 30)
+#define AMC_DUAL_MAX_INNER (1LL << 29)   /* two dates' inner paths index one 32-bit window */
 int amc_dual_upper(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev, int64_t ld,
                    const double *coef_dev, int64_t n_inner, uint64_t inner_seed, double *res_dev,
                    double *U_dev, void *stream);

@@ -25,7 +25,7 @@ AMC_FP64, AMC_MIXED = 0, 1
 AMC_RES_DOUBLES = 8
 AMC_COEF_STRIDE = 5
 AMC_DUAL_MAX_WORK = 1 << 40
-AMC_DUAL_MAX_INNER = 1 << 30
+AMC_DUAL_MAX_INNER = 1 << 29
 AMC_MAX_STEPS = 512
 
 

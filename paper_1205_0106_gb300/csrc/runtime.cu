@@ -221,6 +221,19 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
 
 // Valuation of caller paths with a given boundary (one streaming launch and
 // its finalize; the grid covers 8 paths per thread, at most gcap CTAs).
+// Context scratch of `count` doubles, grown on demand (a cudaFree and a
+// cudaMalloc, which synchronise the device once); *have tracks the size in
+// units of `per` doubles.
+int grow_scratch(double **buf, int64_t *have, int64_t need, size_t per) {
+    if (need <= *have) return AMC_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, sizeof(double) * per * (size_t)need) != cudaSuccess) return AMC_ENOMEM;
+    *have = need;
+    return AMC_OK;
+}
+
 int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, const double *coef, double *res,
              cudaStream_t st) {
     AMC_TRY(host_validate(o));
@@ -236,13 +249,7 @@ int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     J.ld = ld;
     J.coef = const_cast<double *>(coef);
     const int64_t ctas = value_ctas(o->n_paths);
-    if (ctas > c->finv_ctas) {                        // grown on demand (synchronises the device once)
-        cudaFree(c->finv);
-        c->finv = nullptr;
-        c->finv_ctas = 0;
-        if (cudaMalloc(&c->finv, sizeof(double) * 4 * (size_t)ctas) != cudaSuccess) return AMC_ENOMEM;
-        c->finv_ctas = ctas;
-    }
+    AMC_TRY(grow_scratch(&c->finv, &c->finv_ctas, ctas, 4));
     J.n_cta = (int)ctas;
     J.fin = c->finv;
     J.res = res;
@@ -286,13 +293,7 @@ int do_fused(amc_ctx *c, const amc_option *o, int prec, const double *coef, doub
     const int mode = lsm ? kBoundary : (o->rule == AMC_RULE_PAPER_UB ? kPaperRule : kEuropean);
     int64_t grid = 0;
     AMC_TRY_CUDA(pathgen_fused_grid(a, mode, prec == AMC_FP64, c->sm_count, &grid));
-    if (grid > c->finv_ctas) {                        // grown on demand (synchronises the device once)
-        cudaFree(c->finv);
-        c->finv = nullptr;
-        c->finv_ctas = 0;
-        if (cudaMalloc(&c->finv, sizeof(double) * 4 * (size_t)grid) != cudaSuccess) return AMC_ENOMEM;
-        c->finv_ctas = grid;
-    }
+    AMC_TRY(grow_scratch(&c->finv, &c->finv_ctas, grid, 4));
     J.fin = c->finv;
     J.n_cta = (int)grid;
     AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
@@ -320,13 +321,7 @@ int do_dual(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld
     J.coef = const_cast<double *>(coef);
     J.res = res;
     J.status = c->status1;
-    if (o->n_paths > c->dualw_n) {                    // grown on demand (synchronises the device once)
-        cudaFree(c->dualw);
-        c->dualw = nullptr;
-        c->dualw_n = 0;
-        if (cudaMalloc(&c->dualw, sizeof(double) * 3 * (size_t)o->n_paths) != cudaSuccess) return AMC_ENOMEM;
-        c->dualw_n = o->n_paths;
-    }
+    AMC_TRY(grow_scratch(&c->dualw, &c->dualw_n, o->n_paths, 3));
     a.n_in = n_in;
     a.seed_in = seed_in;
     a.L1 = c->dualw;

@@ -218,6 +218,7 @@ def test_dual_rejects_bad_arguments(amc, ctx, torch):
         (opt, 0),                                                          # no inner paths
         (workloads.Option(**{**opt.as_dict(), "rule": 1}), 8),             # not an LSM boundary
         (opt, amc.AMC_DUAL_MAX_WORK // (1000 * 45) + 1),                   # beyond the work bound
+        (workloads.Option(**{**opt.as_dict(), "n_steps": 1, "n_paths": 1}), amc.AMC_DUAL_MAX_INNER + 1),
     ]
     for o, n_in in bad:
         with pytest.raises(amc.AmcError) as ei:
