@@ -415,6 +415,46 @@ def fused_bench(amc, ctx, torch, stream, popt, reps, warmup):
             "workload": "Eqs. 10-11 on the 2^20 x 252 points of shift seed 2, no path array"}
 
 
+def large_bench(amc, ctx, torch, stream, hbm, peak_kind, reps=3, warmup=1):
+    """An option too large for the register-resident LSM sweep: 2^22 paths x
+    252 dates (4.2 GB of FP32 paths), priced by path generation and the
+    streaming sweep (cash flows in device memory, one pass and one solve per
+    date), timed with CUDA events on their stream; the streaming sweep alone
+    against its algorithmic traffic (S_j and S_{j+1} read, the cash flows
+    read and written: 16 bytes per path and date)."""
+    opt = workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 252, 2 ** 22, basis=4, type=workloads.PUT, seed=2)
+    ld = amc.amc_path_ld(opt.n_paths)
+    S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
+    res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: amc.amc_price_device(ctx, opt, amc.AMC_MIXED, S, res, stream=stream))
+    price = amc.res_to_dict(res.cpu().numpy())
+    ms_sweep = timed(lambda: amc.amc_sweep(ctx, opt, amc.AMC_MIXED, S, res, stream=stream))
+    units = opt.n_paths * opt.n_steps
+    nbytes = 16.0 * opt.n_paths * (opt.n_steps - 1)
+    gbs = nbytes / (ms_sweep * 1e-3) / 1e9
+    del S
+    return {"ms": ms, "value": units / (ms * 1e-3), "unit": METRIC, "price": price["price"],
+            "std_err": price["std_err"], "sweep_ms": ms_sweep,
+            "roofline_sweep": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                               "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
+            "workload": "put S0 100 K 100 r 0.05 sigma 0.3 T 1, 2^22 paths x 252 dates, basis 4, shift seed 2, "
+                        "mixed: above the register-resident sweep's 1.17 M paths"}
+
+
 TABLE2_PATHS = (10, 100, 1000, 10000, 100000, 200000, 300000, 500000, 1000000)
 TABLE2_OPTION = dict(S0=36.0, K=40.0, r=0.06, sigma=0.2, T=1.0, n_steps=10, basis=3, type=0, seed=1)
 
@@ -683,6 +723,22 @@ def run_amc(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    if args.profile_large:
+        # profiling mode: the streaming LSM sweep of a 2^21-path, 50-date put (for ncu launch lists)
+        lopt = workloads.Option(100.0, 100.0, 0.05, 0.3, 1.0, 50, 2 ** 21, basis=4, type=workloads.PUT, seed=2)
+        S = torch.empty((lopt.n_steps, amc.amc_path_ld(lopt.n_paths)), dtype=torch.float32, device="cuda")
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            amc.amc_generate_paths(ctx, lopt, amc.AMC_MIXED, S, stream=stream)
+            for _ in range(args.warmup + args.steps):
+                amc.amc_sweep(ctx, lopt, amc.AMC_MIXED, S, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "large", "steps": args.steps, "warmup": args.warmup}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile_fused:
         # profiling mode: only the paper rule priced with no path array (for ncu)
         popt = workloads.Option(**{**opt.as_dict(), "rule": workloads.RULE_PAPER_UB})
@@ -795,6 +851,7 @@ def run_amc(args):
         line["paper_rule"] = paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
         line["randomization"] = randomization_bench(amc, ctx, torch, stream, opt)
         line["dual"] = dual_bench(amc, ctx, torch, stream, opt)
+        line["large"] = large_bench(amc, ctx, torch, stream, hbm, peak_kind)
     if args.serve_seconds > 0:
         times, sopts = workloads.serving_requests(rate=2000.0, duration=args.serve_seconds, seed=4)
         sctx = amc.Context(local, arena_bytes=24 << 30)
@@ -835,6 +892,8 @@ def main():
                     help="run only the paper-rule sweeps (for ncu captures)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only the 4096-option batch, twice (for ncu launch lists)")
+    ap.add_argument("--profile-large", action="store_true",
+                    help="run only the streaming LSM sweep of a 2^21-path option (for ncu launch lists)")
     ap.add_argument("--profile-fused", action="store_true",
                     help="run only the paper rule priced with no path array (for ncu captures)")
     ap.add_argument("--profile-dual", action="store_true",
@@ -844,7 +903,7 @@ def main():
                     help="length of the Poisson serving replay reported under 'serving' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and not (args.profile or args.profile_value or args.profile_paper or args.profile_batch
-                                or args.profile_dual or args.profile_fused):
+                                or args.profile_dual or args.profile_fused or args.profile_large):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

@@ -119,6 +119,10 @@ int amc_ctx_set_timeout(amc_ctx *ctx, double seconds);
  *           at exercise date `arg`, so the other CTAs' waits run out and the
  *           call returns AMC_ETIMEOUT;
  *   kind 2: the next arena reservation fails (AMC_ENOMEM);
+ *   kind 3: the next LSM sweep runs the streaming sweep of large options
+ *           (cash flows in device memory, one pass and one solve per date)
+ *           whatever its path count, so that it can be tested on small
+ *           options;
  *   kind 0: clear.                                                          */
 int amc_ctx_inject(amc_ctx *ctx, int kind, int64_t arg);
 /* Bytes of the arena currently free / total.                               */
@@ -176,7 +180,12 @@ int amc_generate_paths_permuted(amc_ctx *ctx, const amc_option *opt, int prec,
 int amc_lcg_params(uint64_t seed, int n_dims, int64_t n_points, uint32_t *a, uint32_t *c, uint64_t *M);
 /* Step 4 on caller paths S (as written by amc_generate_paths), result into
  * res_dev[AMC_RES_DOUBLES].  with_greeks != 0 also fills delta and vega
- * (frozen exercise boundary).  Asynchronous.                               */
+ * (frozen exercise boundary).  Asynchronous.  An LSM option with more paths
+ * than the register-resident sweep holds (about 1.2 M on 152 SMs) runs the
+ * streaming sweep: its cash flows in context memory, one pass and one solve
+ * per date (16 bytes of traffic per path and date); the pathwise rules run
+ * on a larger grid.  Greeks, batches and serving keep the register-resident
+ * sizes (AMC_EINVAL beyond them).                                          */
 int amc_sweep(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_dev,
               int64_t ld, int with_greeks, double *res_dev, void *stream);
 /* Steps 1-4 into caller storage: amc_generate_paths then amc_sweep.        */

@@ -65,6 +65,8 @@ struct amc_ctx {
     int64_t finv_ctas = 0;
     double *dualw = nullptr;                         // per-path L_1, V and inner steps of the dual upper bound (grown on demand)
     int64_t dualw_n = 0;
+    double *streamw = nullptr;                       // streaming LSM sweep: cash flows, partials, coefficients (grown on demand)
+    int64_t streamw_n = 0;
     uint64_t *xch1 = nullptr;                        // exchange units of the mixed LSM sweep
     uint32_t epoch = 0;                              // launch tag of those units
     int gcap = 0;

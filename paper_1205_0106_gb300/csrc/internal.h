@@ -163,6 +163,22 @@ size_t pathgen_smem_bytes(int max_m, int nslots, bool fp64);
 cudaError_t ensure_smem(const void *f, size_t smem);
 cudaError_t ctas_per_sm(const void *f, int threads, size_t smem, int *out);
 
+// Streaming LSM sweep for options whose per-path state does not fit on chip
+// (sweep_stream.cu): the option, its paths S [m][ld], result block, status
+// and optional boundary output in `one`; scratch in device memory.
+struct StreamArgs {
+    Job one;
+    void *cf;                       // [ld] cash flows (units of K), Real
+    double *part;                   // [grid][kNV] per-CTA partial sums of the current date
+    double *beta;                   // [m][4] coefficients (units of K) of dates 1..m
+    int32_t *deg;                   // [m] degenerate flags
+    int32_t *ndeg;                  // degenerate dates so far
+    int32_t grid;                   // CTAs of every pass
+};
+constexpr int kStreamThreads = 256;
+int64_t stream_grid(int sm_count, bool fp64, bool put);
+cudaError_t launch_lsm_stream(const StreamArgs &a, bool fp64, cudaStream_t st);
+
 // Dual upper bound of a fitted boundary (dual.cu): the option, its outer
 // paths S [m][ld], boundary coef, result block and status word in `one`.
 struct DualArgs {

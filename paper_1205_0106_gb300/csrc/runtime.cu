@@ -115,6 +115,19 @@ int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, boo
     return AMC_OK;
 }
 
+// Context scratch of `count` doubles, grown on demand (a cudaFree and a
+// cudaMalloc, which synchronise the device once); *have tracks the size in
+// units of `per` doubles.
+int grow_scratch(double **buf, int64_t *have, int64_t need, size_t per) {
+    if (need <= *have) return AMC_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, sizeof(double) * per * (size_t)need) != cudaSuccess) return AMC_ENOMEM;
+    *have = need;
+    return AMC_OK;
+}
+
 int check_prec(int prec) { return (prec == AMC_FP64 || prec == AMC_MIXED) ? AMC_OK : AMC_EINVAL; }
 
 // Caller path storage: rows must start on 16-byte boundaries for the
@@ -177,6 +190,45 @@ int do_generate_permuted(amc_ctx *c, const amc_option *o, int prec, void *S, int
     return AMC_OK;
 }
 
+// LSM sweep of an option too large for the register-resident sweeps: one
+// streaming pass and one solve per date, scratch in context memory.
+int do_sweep_stream(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, double *res,
+                    cudaStream_t st, double *coef) {
+    const bool fp64 = prec == AMC_FP64;
+    StreamArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    Job &J = sa.one;
+    fill_job_common(o, &J);
+    J.S = const_cast<void *>(S);
+    J.ld = ld;
+    J.res = res;
+    J.status = c->status1;
+    J.coef = coef;
+    const int64_t grid = stream_grid(c->sm_count, fp64, o->type == AMC_PUT);
+    // cash flows [ld] (up to 8 bytes each), partials [grid][kNV], coefficients
+    // [AMC_MAX_STEPS][4], then degenerate flags and count (int32, in doubles)
+    const int64_t n_flags = (AMC_MAX_STEPS + 2) / 2;
+    AMC_TRY(grow_scratch(&c->streamw, &c->streamw_n, ld + grid * kNV + (int64_t)AMC_MAX_STEPS * 4 + n_flags, 1));
+    sa.cf = c->streamw;
+    sa.part = c->streamw + ld;
+    sa.beta = sa.part + grid * kNV;
+    sa.deg = reinterpret_cast<int32_t *>(sa.beta + (int64_t)AMC_MAX_STEPS * 4);
+    sa.ndeg = sa.deg + AMC_MAX_STEPS;
+    sa.grid = (int32_t)grid;
+    AMC_TRY(grow_scratch(&c->finv, &c->finv_ctas, grid, 4));
+    J.fin = c->finv;
+    J.n_cta = (int)grid;
+    AMC_TRY_CUDA(cudaMemsetAsync(sa.deg, 0, sizeof(int32_t) * (AMC_MAX_STEPS + 1), st));
+    AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
+    AMC_TRY_CUDA(launch_lsm_stream(sa, fp64, st));
+    KArgs &a = c->args;
+    memset(&a, 0, sizeof(KArgs));
+    a.one = J;
+    a.n_jobs = 1;
+    AMC_TRY_CUDA(launch_finalize(a, st));
+    return AMC_OK;
+}
+
 int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, bool greeks, double *res,
              cudaStream_t st, double *coef = nullptr) {
     AMC_TRY(host_validate(o));
@@ -184,9 +236,21 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     AMC_TRY(check_storage(S, ld, o->n_paths));
     if (!res || ((uintptr_t)res & 7u) != 0) return AMC_EINVAL;
     if (greeks && o->rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
+    if (c->inject_kind == 3 && o->rule == AMC_RULE_LSM && !greeks) {
+        c->inject_kind = 0;
+        return do_sweep_stream(c, o, prec, S, ld, res, st, coef);
+    }
     SweepPlan pl;
-    AMC_TRY(host_plan_sweep(o->n_paths, c->sm_count, prec, o->rule, &pl));
-    if (pl.ctas > c->gcap) return AMC_EINVAL;
+    bool big = false;                                 // too many paths for the co-resident plans
+    if (host_plan_sweep(o->n_paths, c->sm_count, prec, o->rule, &pl) != AMC_OK || pl.ctas > c->gcap) {
+        if (greeks) return AMC_EINVAL;                // frozen-boundary Greeks: register-resident sizes only
+        if (o->rule == AMC_RULE_LSM) return do_sweep_stream(c, o, prec, S, ld, res, st, coef);
+        // the pathwise rules need no co-resident CTAs: any grid, 8 paths per thread
+        pl.kind = 1;
+        pl.chunks = 2;
+        pl.ctas = (int)((o->n_paths + (int64_t)kSweepThreads * 8 - 1) / ((int64_t)kSweepThreads * 8));
+        big = true;
+    }
     KArgs &a = c->args;
     memset(&a, 0, sizeof(KArgs));
     Job &J = a.one;
@@ -200,6 +264,10 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     J.part = c->part1;
     J.arrive = c->arrive1;
     J.fin = c->fin1;
+    if (big) {
+        AMC_TRY(grow_scratch(&c->finv, &c->finv_ctas, pl.ctas, 4));
+        J.fin = c->finv;
+    }
     J.res = res;
     J.status = c->status1;
     J.xch = c->xch1;
@@ -221,19 +289,6 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
 
 // Valuation of caller paths with a given boundary (one streaming launch and
 // its finalize; the grid covers 8 paths per thread, at most gcap CTAs).
-// Context scratch of `count` doubles, grown on demand (a cudaFree and a
-// cudaMalloc, which synchronise the device once); *have tracks the size in
-// units of `per` doubles.
-int grow_scratch(double **buf, int64_t *have, int64_t need, size_t per) {
-    if (need <= *have) return AMC_OK;
-    cudaFree(*buf);
-    *buf = nullptr;
-    *have = 0;
-    if (cudaMalloc(buf, sizeof(double) * per * (size_t)need) != cudaSuccess) return AMC_ENOMEM;
-    *have = need;
-    return AMC_OK;
-}
-
 int do_value(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, const double *coef, double *res,
              cudaStream_t st) {
     AMC_TRY(host_validate(o));
@@ -704,6 +759,7 @@ int amc_ctx_destroy(amc_ctx *c) {
     cudaFree(c->fin1);
     cudaFree(c->finv);
     cudaFree(c->dualw);
+    cudaFree(c->streamw);
     cudaFree(c->res1);
     cudaFree(c->status1);
     cudaFree(c->xch1);
@@ -727,7 +783,7 @@ int amc_ctx_set_timeout(amc_ctx *c, double seconds) {
 }
 
 int amc_ctx_inject(amc_ctx *c, int kind, int64_t arg) {
-    if (!c || kind < 0 || kind > 2) return AMC_EINVAL;
+    if (!c || kind < 0 || kind > 3) return AMC_EINVAL;
     c->inject_kind = kind;
     c->inject_arg = arg;
     return AMC_OK;

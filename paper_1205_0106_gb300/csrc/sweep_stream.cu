@@ -1,0 +1,354 @@
+// Longstaff-Schwartz backward sweep (ref. [12], the backward induction of
+// §V) for options whose per-path state does not fit on chip: the cash flows
+// live in device memory and every exercise date is one streaming pass plus
+// one small solve, so any path count runs (the register-resident sweeps
+// need all their CTAs resident at once, which caps them near 1.2 M paths).
+//
+//   pass(j), j = m-1 .. 1 (grid-stride over groups of 4 consecutive paths,
+//   16-byte row loads):
+//     j = m-1: CF = h(S_m) / K; otherwise CF is read, and the paths that the
+//       boundary of date j+1 exercises (not degenerate, in the money,
+//       h > c_{j+1}(y)) take CF = h(S_{j+1}) / K;
+//     CF <- e^{-r dt} CF, written back;
+//     the in-the-money moments sum y^k (k = 0..2p-2) and right-hand sides
+//       sum y^k CF (k < p) of date j, y = S_j / K - 1, per thread in
+//       compensated FP32, then double-float (FP32 pairs) through the warp
+//       and CTA trees into the CTA's partial row (FP64 throughout under
+//       AMC_FP64: this GPU's FP64 pipe is slow enough that a tree of
+//       doubles would cost more than the pass's memory traffic);
+//   solve(j) (one CTA): the partial rows added in a fixed order (double-
+//     float, then FP64 for the solve),
+//     the equilibrated Cholesky solve, beta_j or the degenerate flag (fewer
+//     than p paths in the money, or a pivot <= 1e-12), and the boundary row;
+//   final pass: the exercise of date 1 (or CF = h(S_1) / K when m = 1), then
+//     per-CTA FP64 sums of CF and CF^2 for finalize_kernel, which applies the
+//     last e^{-r dt}.
+// Traffic per path and date: S_j and S_{j+1} read, CF read and written
+// (16 bytes in FP32).  Deterministic: fixed grid, fixed path ranges, fixed
+// reduction order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "devutil.cuh"
+#include "internal.h"
+#include "lsm_solve.cuh"
+
+namespace amc {
+
+namespace {
+
+template <bool FP64>
+struct ST;
+template <>
+struct ST<false> {
+    using Real = float;
+};
+template <>
+struct ST<true> {
+    using Real = double;
+};
+
+__device__ __forceinline__ void ld4(const float *p, float *o) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double *o) {
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double *v) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Fixed-order FP64 sum of NV values over the CTA (kStreamThreads threads);
+// thread 0 holds the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum_d(double (&v)[NV], double (*red)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < kStreamThreads / 32; ++w) t += red[w][k];
+            v[k] = t;
+        }
+}
+
+// Compensated accumulation (Kahan; FP32 adds that FMA contraction cannot
+// merge).  In FP64 a plain sum.
+template <bool FP64>
+struct Acc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ dev::dfl get_df() const { return dev::df_add({s, 0.f}, {-c, 0.f}); }
+};
+template <>
+struct Acc<true> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// Per-CTA totals of the kNV accumulators, in thread 0.  FP32 path: double-
+// float through the warp tree and the CTA (the FP64 pipe of this GPU is
+// slow; a tree of doubles here costs more than the pass's memory traffic);
+// FP64 path: doubles.  Fixed order in both.
+struct DfRed {
+    dev::dfl w[kStreamThreads / 32][kNV];
+};
+struct DRed {
+    double w[kStreamThreads / 32][kNV];
+};
+__device__ __forceinline__ void cta_totals(Acc<false> (&acc)[kNV], DfRed &red, dev::dfl (&tot)[kNV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) {
+        const dev::dfl d = dev::df_warp_sum(acc[k].get_df());
+        if (lane == 0) red.w[warp][k] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) {
+            dev::dfl t = red.w[0][k];
+            for (int w = 1; w < kStreamThreads / 32; ++w) t = dev::df_add(t, red.w[w][k]);
+            tot[k] = t;
+        }
+}
+__device__ __forceinline__ void cta_totals(Acc<true> (&acc)[kNV], DRed &red, double (&tot)[kNV]) {
+    double v[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) v[k] = acc[k].get();
+    block_sum_d<kNV>(v, red.w);
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) tot[k] = v[k];
+}
+__device__ __forceinline__ double to_d(dev::dfl x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+
+
+// One exercise date: j = 1 .. m-1 sums the moments of date j; j = 0 is the
+// final pass (exercise of date 1, sums of CF).
+template <bool FP64, bool PUT>
+__global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_constant__ StreamArgs a, int j) {
+    using Real = typename ST<FP64>::Real;
+    using Red = typename std::conditional<FP64, DRed, DfRed>::type;
+    using Tot = typename std::conditional<FP64, double, dev::dfl>::type;
+    __shared__ Red red;
+    const Job &J = a.one;
+    const int m = J.m, p = J.p;
+    const int64_t N = J.N, ld = J.ld;
+    const Real *__restrict__ S = reinterpret_cast<const Real *>(J.S);
+    Real *__restrict__ cf = reinterpret_cast<Real *>(a.cf);
+    const Real invK = (Real)J.invK, disc = (Real)J.disc;
+    // exercise boundary of date j+1 (row j), unless the pass starts at maturity
+    const int ed = j + 1;                                   // date whose boundary this pass applies
+    const bool init = (j == m - 1) || (m == 1);
+    const bool exer = !init && ed <= m - 1 && !a.deg[ed - 1];
+    Real c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    if (exer) {
+        c0 = (Real)a.beta[(ed - 1) * 4 + 0];
+        c1 = (Real)a.beta[(ed - 1) * 4 + 1];
+        c2 = (Real)a.beta[(ed - 1) * 4 + 2];
+        c3 = (Real)a.beta[(ed - 1) * 4 + 3];
+    }
+    Acc<FP64> acc[kNV];
+    const int64_t groups = (N + 3) / 4;
+#pragma unroll 2
+    for (int64_t g = (int64_t)blockIdx.x * kStreamThreads + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * kStreamThreads) {
+        const int64_t i0 = 4 * g;
+        Real v[4], s[4], sj[4];
+        if (j >= 1) ld4(S + (int64_t)(j - 1) * ld + i0, sj);     // S_j, issued with the other rows
+        if (init) {
+            ld4(S + (int64_t)(m - 1) * ld + i0, s);         // S_m
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const Real y = fma(s[e], invK, Real(-1));
+                const Real h = PUT ? -y : y;
+                v[e] = h > Real(0) ? h : Real(0);
+            }
+        } else {
+            ld4(cf + i0, v);
+            if (exer) {
+                ld4(S + (int64_t)(ed - 1) * ld + i0, s);    // S_{j+1}
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const Real y = fma(s[e], invK, Real(-1));
+                    const Real h = PUT ? -y : y;
+                    const Real cont = fma(fma(fma(c3, y, c2), y, c1), y, c0);
+                    if ((PUT ? y < Real(0) : y > Real(0)) && h > cont) v[e] = h;
+                }
+            }
+        }
+        if (j >= 1) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] *= disc;
+            st4(cf + i0, v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (i0 + e >= N) continue;
+                const Real y = fma(sj[e], invK, Real(-1));
+                if (!(PUT ? y < Real(0) : y > Real(0))) continue;      // in the money, strictly
+                Real pw = Real(1);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    if (k < 2 * p - 1) acc[k].add(pw);
+                    if (k < p) acc[7 + k].add(pw * v[e]);
+                    pw *= y;
+                }
+            }
+        } else {
+            // final pass: the cash flow at t_1 (finalize applies the last discount)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (i0 + e >= N) continue;
+                acc[0].add(v[e]);
+                acc[1].add(v[e] * v[e]);
+            }
+        }
+    }
+    Tot tot[kNV];
+    cta_totals(acc, red, tot);
+    if (threadIdx.x == 0) {
+        if (j >= 1) {
+            Tot *row = reinterpret_cast<Tot *>(a.part) + (int64_t)blockIdx.x * kNV;
+#pragma unroll
+            for (int k = 0; k < kNV; ++k) row[k] = tot[k];
+        } else {
+            double *fin = reinterpret_cast<double *>(J.fin) + (int64_t)blockIdx.x * 4;
+            fin[0] = J.K * to_d(tot[0]);
+            fin[1] = J.K * J.K * to_d(tot[1]);
+            fin[2] = 0.0;
+            fin[3] = 0.0;
+            if (blockIdx.x == 0) J.res[4] = (double)*a.ndeg;
+        }
+    }
+}
+
+// Solve of date j from the partial rows: fixed-order FP64 sums (thread t
+// adds rows t, t + kStreamThreads, ..), a fixed tree, then one thread.
+template <bool FP64>
+__global__ void __launch_bounds__(kStreamThreads) lsm_stream_solve(const __grid_constant__ StreamArgs a, int j) {
+    const Job &J = a.one;
+    const int p = J.p;
+    double tot[kNV];
+    if constexpr (FP64) {
+        __shared__ double red[kStreamThreads / 32][kNV];
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) tot[k] = 0.0;
+        for (int c = threadIdx.x; c < a.grid; c += kStreamThreads) {
+            const double *row = a.part + (int64_t)c * kNV;
+#pragma unroll
+            for (int k = 0; k < kNV; ++k) tot[k] += row[k];
+        }
+        block_sum_d<kNV>(tot, red);
+    } else {
+        __shared__ DfRed red;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        dev::dfl t[kNV];
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) t[k] = {0.f, 0.f};
+        for (int c = threadIdx.x; c < a.grid; c += kStreamThreads) {
+            const dev::dfl *row = reinterpret_cast<const dev::dfl *>(a.part) + (int64_t)c * kNV;
+#pragma unroll
+            for (int k = 0; k < kNV; ++k) t[k] = dev::df_add(t[k], row[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) {
+            const dev::dfl d = dev::df_warp_sum(t[k]);
+            if (lane == 0) red.w[warp][k] = d;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < kNV; ++k) {
+                dev::dfl u = red.w[0][k];
+                for (int w = 1; w < kStreamThreads / 32; ++w) u = dev::df_add(u, red.w[w][k]);
+                tot[k] = to_d(u);
+            }
+    }
+    if (threadIdx.x != 0) return;
+    double beta[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool ok = tot[0] >= (double)p && solve_normal(p, tot, tot + 7, beta);
+    a.deg[j - 1] = ok ? 0 : 1;
+    if (!ok) *a.ndeg += 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.beta[(j - 1) * 4 + k] = ok ? beta[k] : 0.0;
+    if (J.coef) {
+        double *c = J.coef + (size_t)(j - 1) * kCoefStride;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = ok ? beta[k] : 0.0;
+        c[4] = ok ? 0.0 : 1.0;
+        if (j == J.m - 1) {                                 // maturity: no exercise decision
+            double *cm = J.coef + (size_t)(J.m - 1) * kCoefStride;
+            cm[0] = cm[1] = cm[2] = cm[3] = 0.0;
+            cm[4] = 1.0;
+        }
+    }
+}
+
+__global__ void lsm_stream_coef_m1(const __grid_constant__ StreamArgs a) {
+    // m = 1: only the maturity row of the boundary
+    if (threadIdx.x == 0 && a.one.coef) {
+        double *cm = a.one.coef;
+        cm[0] = cm[1] = cm[2] = cm[3] = 0.0;
+        cm[4] = 1.0;
+    }
+}
+
+}  // namespace
+
+namespace {
+using PassFn = void (*)(StreamArgs, int);
+PassFn pass_fn(bool fp64, bool put) {
+    return fp64 ? (put ? lsm_stream_pass<true, true> : lsm_stream_pass<true, false>)
+                : (put ? lsm_stream_pass<false, true> : lsm_stream_pass<false, false>);
+}
+}  // namespace
+
+// As many CTAs as fit on the SMs at once.
+int64_t stream_grid(int sm_count, bool fp64, bool put) {
+    int per = 0;
+    if (ctas_per_sm((const void *)pass_fn(fp64, put), kStreamThreads, 0, &per) != cudaSuccess || per < 1) per = 1;
+    return (int64_t)per * sm_count;
+}
+
+cudaError_t launch_lsm_stream(const StreamArgs &a, bool fp64, cudaStream_t st) {
+    const Job &J = a.one;
+    const PassFn pass = pass_fn(fp64, J.type == AMC_PUT);
+    const unsigned g = (unsigned)a.grid;
+    if (J.m == 1) {
+        lsm_stream_coef_m1<<<1, 32, 0, st>>>(a);
+    } else {
+        for (int j = J.m - 1; j >= 1; --j) {
+            pass<<<g, kStreamThreads, 0, st>>>(a, j);
+            if (fp64) lsm_stream_solve<true><<<1, kStreamThreads, 0, st>>>(a, j);
+            else lsm_stream_solve<false><<<1, kStreamThreads, 0, st>>>(a, j);
+        }
+    }
+    pass<<<g, kStreamThreads, 0, st>>>(a, 0);
+    return cudaGetLastError();
+}
+
+}  // namespace amc
