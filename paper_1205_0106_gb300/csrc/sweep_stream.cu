@@ -17,9 +17,10 @@
 //       AMC_FP64: this GPU's FP64 pipe is slow enough that a tree of
 //       doubles would cost more than the pass's memory traffic);
 //   solve(j) (one CTA): the partial rows added in a fixed order (double-
-//     float, then FP64 for the solve),
-//     the equilibrated Cholesky solve, beta_j or the degenerate flag (fewer
-//     than p paths in the money, or a pivot <= 1e-12), and the boundary row;
+//     float, then FP64), the inverse of the Gram matrix by cofactors over
+//     one warp, beta_j or the degenerate flag (fewer than p paths in the
+//     money, or an equilibrated Cholesky pivot <= 1e-12, decided from the
+//     leading principal minors), and the boundary row;
 //   final pass: the exercise of date 1 (or CF = h(S_1) / K when m = 1), then
 //     per-CTA FP64 sums of CF and CF^2 for finalize_kernel, which applies the
 //     last e^{-r dt}.
@@ -288,9 +289,26 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_solve(const __grid_
                 tot[k] = to_d(u);
             }
     }
-    if (threadIdx.x != 0) return;
-    double beta[4] = {0.0, 0.0, 0.0, 0.0};
-    const bool ok = tot[0] >= (double)p && solve_normal(p, tot, tot + 7, beta);
+    // the inverse of the Gram matrix by cofactors over warp 0 (FP64 chains a
+    // few operations deep: this GPU's FP64 latency makes a one-thread
+    // Cholesky the longest step of a date), then beta_k = sum_l Ginv_kl R_l
+    __shared__ double sM[kNV], sA[16], sP[4];
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) sM[k] = tot[k];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    bool degen = false;
+    const double inv = gram_inverse(sM, p, lane, sA, sP, degen);
+    double t = lane < 16 ? inv * sM[7 + (lane & 3)] : 0.0;
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    double beta[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) beta[k] = __shfl_sync(0xffffffffu, t, 4 * k);
+    if (lane != 0) return;
+    const bool ok = !degen;
     a.deg[j - 1] = ok ? 0 : 1;
     if (!ok) *a.ndeg += 1;
 #pragma unroll
