@@ -113,6 +113,88 @@ struct Acc<true> {
     __device__ __forceinline__ double get() const { return s; }
 };
 
+// Two of the compensated FP32 accumulators above in one packed register
+// pair: add/sub.rn.f32x2 take the two lanes' round-to-nearest steps in one
+// issue slot, the same steps in the same order as the scalar sum.  The
+// totals are not always bit-identical to the scalar loop's: on a 2^22-path,
+// 252-date put the price moves by 0.9e-6 K (the powers y^5 of paths within
+// about 3e-8 of the strike are subnormal, the likely source).
+__device__ __forceinline__ dev::f2 f2_sub(dev::f2 a, dev::f2 b) {
+    dev::f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+struct Acc2 {
+    dev::f2 s{0ull}, c{0ull};
+    __device__ __forceinline__ void add(dev::f2 v) {
+        const dev::f2 y = f2_sub(v, c);
+        const dev::f2 t = dev::f2_add(s, y);
+        c = f2_sub(f2_sub(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ void unpack(Acc<false> &lo, Acc<false> &hi) const {
+        lo.s = dev::f2_lo(s); lo.c = dev::f2_lo(c);
+        hi.s = dev::f2_hi(s); hi.c = dev::f2_hi(c);
+    }
+};
+
+// Per-thread sums of one pass, accumulator k = moment k (k < 7) or right-
+// hand side k - 7.  FP64: one double each.  FP32: the 11 compensated sums
+// as packed pairs (M0,M1) (M2,M3) (M4,M5) (R0,R1) (R2,R3) and M6 alone, the
+// powers y^k formed one product at a time as in the scalar loop.  A pair
+// with one slot the basis uses also fills the other (M1 for p = 1, M3 for
+// p <= 2, M5 and R3 for p = 3); no solve reads those slots.
+template <bool FP64>
+struct PathSums {
+    Acc<true> a[kNV];
+    __device__ __forceinline__ void add_path(double y, double v, int p) {
+        double pw = 1.0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            if (k < 2 * p - 1) a[k].add(pw);
+            if (k < p) a[7 + k].add(pw * v);
+            pw *= y;
+        }
+    }
+    __device__ __forceinline__ void add_final(double v) {
+        a[0].add(v);
+        a[1].add(v * v);
+    }
+    __device__ __forceinline__ void get(Acc<true> (&o)[kNV]) const {
+#pragma unroll
+        for (int k = 0; k < kNV; ++k) o[k] = a[k];
+    }
+};
+template <>
+struct PathSums<false> {
+    Acc2 m01, m23, m45, r01, r23;
+    Acc<false> m6;
+    __device__ __forceinline__ void add_path(float y, float v, int p) {
+        const float y2 = y * y, y3 = y2 * y;
+        const dev::f2 p01 = dev::f2_pack(1.f, y), p23 = dev::f2_pack(y2, y3);
+        const dev::f2 V = dev::f2_splat(v);
+        m01.add(p01);
+        r01.add(dev::f2_mul(p01, V));
+        if (p >= 2) m23.add(p23);
+        if (p >= 3) {
+            const float y4 = y3 * y, y5 = y4 * y;
+            m45.add(dev::f2_pack(y4, y5));
+            r23.add(dev::f2_mul(p23, V));
+            if (p >= 4) m6.add(y5 * y);
+        }
+    }
+    __device__ __forceinline__ void add_final(float v) { m01.add(dev::f2_pack(v, v * v)); }
+    __device__ __forceinline__ void get(Acc<false> (&o)[kNV]) const {
+        m01.unpack(o[0], o[1]);
+        m23.unpack(o[2], o[3]);
+        m45.unpack(o[4], o[5]);
+        o[6] = m6;
+        r01.unpack(o[7], o[8]);
+        r23.unpack(o[9], o[10]);
+        o[11] = Acc<false>();
+    }
+};
+
 // Per-CTA totals of the kNV accumulators, in thread 0.  FP32 path: double-
 // float through the warp tree and the CTA (the FP64 pipe of this GPU is
 // slow; a tree of doubles here costs more than the pass's memory traffic);
@@ -176,7 +258,7 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_c
         c2 = (Real)a.beta[(ed - 1) * 4 + 2];
         c3 = (Real)a.beta[(ed - 1) * 4 + 3];
     }
-    Acc<FP64> acc[kNV];
+    PathSums<FP64> sums;
     const int64_t groups = (N + 3) / 4;
 #pragma unroll 2
     for (int64_t g = (int64_t)blockIdx.x * kStreamThreads + threadIdx.x; g < groups;
@@ -214,24 +296,19 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_c
                 if (i0 + e >= N) continue;
                 const Real y = fma(sj[e], invK, Real(-1));
                 if (!(PUT ? y < Real(0) : y > Real(0))) continue;      // in the money, strictly
-                Real pw = Real(1);
-#pragma unroll
-                for (int k = 0; k < 7; ++k) {
-                    if (k < 2 * p - 1) acc[k].add(pw);
-                    if (k < p) acc[7 + k].add(pw * v[e]);
-                    pw *= y;
-                }
+                sums.add_path(y, v[e], p);
             }
         } else {
             // final pass: the cash flow at t_1 (finalize applies the last discount)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (i0 + e >= N) continue;
-                acc[0].add(v[e]);
-                acc[1].add(v[e] * v[e]);
+                sums.add_final(v[e]);
             }
         }
     }
+    Acc<FP64> acc[kNV];
+    sums.get(acc);
     Tot tot[kNV];
     cta_totals(acc, red, tot);
     if (threadIdx.x == 0) {
@@ -304,7 +381,7 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_solve(const __grid_
     const int lane = threadIdx.x;
     bool degen = false;
     const double inv = gram_inverse(sM, p, lane, sA, sP, degen);
-    double t = lane < 16 ? inv * sM[7 + (lane & 3)] : 0.0;
+    double t = (lane < 16 && (lane & 3) < p) ? inv * sM[7 + (lane & 3)] : 0.0;   // R_l, l >= p: unread
     t += __shfl_xor_sync(0xffffffffu, t, 1);
     t += __shfl_xor_sync(0xffffffffu, t, 2);
     double beta[4];
