@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             }
         }
 
-        // unrolled in the store mode: the quantile of later nodes overlaps the
-        // bridge and store of earlier ones (0.442 -> 0.405 ms on 2^20 x 252)
-#pragma unroll ((MODE == kStore || (MODE == kPaperRule && !FP64)) ? 8 : 1)
+        // FP32 store/paper-rule modes unrolled: later nodes' quantiles overlap earlier nodes' bridge and store
+        // (0.442 -> 0.405 ms on 2^20 x 252); FP64 stays rolled (unrolled by 8: 69 -> 106 ms all-FP64 pricing)
+#pragma unroll ((!FP64 && (MODE == kStore || MODE == kPaperRule)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
             const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];
