@@ -12,7 +12,8 @@
 //     CF <- e^{-r dt} CF, written back;
 //     the in-the-money moments sum y^k (k = 0..2p-2) and right-hand sides
 //       sum y^k CF (k < p) of date j, y = S_j / K - 1, per thread in
-//       compensated FP32, then double-float (FP32 pairs) through the warp
+//       compensated FP32 (two sums per packed f32x2 register pair), then
+//       double-float (FP32 pairs) through the warp
 //       and CTA trees into the CTA's partial row (FP64 throughout under
 //       AMC_FP64: this GPU's FP64 pipe is slow enough that a tree of
 //       doubles would cost more than the pass's memory traffic);
