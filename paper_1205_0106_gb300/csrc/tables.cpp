@@ -191,7 +191,7 @@ int host_validate(const amc_option *o) {
 int64_t host_ld(int64_t n_paths) { return (n_paths + 31) / 32 * 32; }
 
 // Sweep launch plan of one option.  Mixed-precision LSM: one 1024-thread
-// CTA per 7936 paths, at most one CTA per SM (co-resident).  Otherwise:
+// CTA per 7680 paths, at most one CTA per SM (co-resident).  Otherwise:
 // CTAs of kSweepThreads threads, each thread owning `chunks` groups of 4
 // consecutive paths, the fewest chunks per thread (1, 2, 4, 8) whose CTA
 // count fits the co-resident capacity sweep_ctas_per_sm(chunks) * SMs.

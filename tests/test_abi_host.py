@@ -80,11 +80,24 @@ def test_validation(amc):
     import workloads
     good = workloads.single_small()
     assert amc.amc_validate_option(good) == 0
-    for field, bad in [("S0", 0.0), ("K", -1.0), ("sigma", float("nan")), ("T", 0.0), ("r", float("inf")),
-                       ("n_steps", 0), ("n_steps", 513), ("n_paths", 0), ("basis", 5), ("type", 2), ("rule", 3)]:
+    inf, nan = float("inf"), float("nan")
+    for field, bad in [("S0", 0.0), ("S0", -36.0), ("S0", inf), ("S0", nan), ("K", -1.0), ("K", 0.0), ("K", inf),
+                       ("sigma", nan), ("sigma", 0.0), ("sigma", -0.2), ("sigma", inf), ("T", 0.0), ("T", -1.0),
+                       ("T", inf), ("r", inf), ("r", -inf), ("r", nan), ("n_steps", 0), ("n_steps", -1),
+                       ("n_steps", 513), ("n_paths", 0), ("n_paths", -5), ("n_paths", 2 ** 31 + 1), ("basis", 0),
+                       ("basis", 5), ("type", 2), ("type", -1), ("rule", 3), ("rule", -1)]:
         d = good.as_dict()
         d[field] = bad
-        assert amc.amc_validate_option(d) == amc.AMC_EINVAL, field
+        assert amc.amc_validate_option(d) == amc.AMC_EINVAL, (field, bad)
+    # the limits themselves are valid, as are a negative rate and, outside LSM, any basis
+    for field, ok in [("n_steps", 1), ("n_steps", 512), ("n_paths", 1), ("n_paths", 2 ** 31), ("basis", 1),
+                      ("basis", 4), ("r", -0.02), ("r", 0.0)]:
+        d = good.as_dict()
+        d[field] = ok
+        assert amc.amc_validate_option(d) == 0, (field, ok)
+    for rule in (amc.AMC_RULE_PAPER_UB, amc.AMC_RULE_EUROPEAN):
+        d = dict(good.as_dict(), rule=rule, basis=0)
+        assert amc.amc_validate_option(d) == 0, rule
 
 
 def test_path_layout(amc):
