@@ -53,7 +53,7 @@ constexpr int kSweepThreads = 256;
 constexpr int sweep_ctas_per_sm(int chunks) { return chunks <= 2 ? 4 : (chunks == 4 ? 2 : 1); }
 // kind 1: generic sweep kernels (sweep.cu: FP64 LSM and the pathwise
 // rules), `chunks` 4-path chunks per thread, 256 threads per CTA;
-// kind 2: mixed-precision LSM kernel (sweep_v2.cu), 7936 paths per CTA.
+// kind 2: mixed-precision LSM kernel (sweep_v2.cu), 7680 paths per CTA.
 struct SweepPlan {
     int kind;
     int chunks;
