@@ -7,9 +7,9 @@
 // j = m-1..1:
 //   read S[j-1][own paths] once (float4, streaming), CF *= e^{-r dt};
 //   per-thread plain sums over the own paths of the in-the-money moments
-//   M_k = sum x^k (k < 2p-1) and right-hand sides R_k = sum x^k CF (k < p),
-//   x = S/K, then a warp shuffle tree, then double-float (compensated FP32)
-//   sums across warps and across the CTAs of the group in a fixed order;
+//   M_k = sum y^k (k < 2p-1) and right-hand sides R_k = sum y^k CF (k < p),
+//   y = S/K - 1, then a warp shuffle tree, then double-float (FP32 pairs;
+//   doubles in FP64) across warps and the group's CTAs in a fixed order;
 //   every CTA of the group reads all CTA partials once the date's arrival
 //   counter is complete and reduces them the same way, so all CTAs obtain
 //   bit-identical totals, solve the equilibrated normal equations in FP64
