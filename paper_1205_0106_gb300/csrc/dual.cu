@@ -21,8 +21,8 @@
 // dual_inner_kernel: one CTA per outer path.  Warps take dates in snake
 // order (most work first) and run their inner paths as a queue shared
 // by the warp's lanes (a lane whose path stops takes the next path at once,
-// across the boundary between two dates), with FP64 sums per lane added in
-// a fixed tree, so Q_j does not depend on which warp or lane ran what.  One
+// across the boundary between two dates); per-lane sums (FP32 in mixed precision) meet in an FP64
+// warp tree, and paths go to lanes in an order fixed by the data, so Q_j does not depend on timing.  One
 // thread then forms L_1 and V(i) = max_j (Z_j - (M_j + L0)), so that
 // U(i) = L0 + V(i).
 // dual_final_kernel: one CTA reduces L_1 to L0 and V to the mean and the
