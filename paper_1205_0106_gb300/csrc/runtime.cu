@@ -1,7 +1,9 @@
 // C ABI runtime of the amc library: contexts, the device arena, option
 // validation, job packing and the launch sequence of the hot path
-// (path generation -> sweep -> finalize).  Everything that computes runs in
-// the kernels of pathgen.cu and sweep.cu; this file only plans and launches.
+// (path generation -> sweep -> finalize) and of the second pass, the dual
+// bound and the no-path-array pricing.  Everything that computes runs in the
+// kernels of pathgen.cu, sweep_v2.cu, sweep.cu, sweep_stream.cu, value.cu
+// and dual.cu; this file only plans and launches.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
