@@ -1,7 +1,8 @@
 """FP64 CPU oracle for the QMC American-option hot path.
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
-CPU-baseline leg of bench.py, never by the product library.  It shares no
+CPU-baseline leg and the reference arm of bench.py, never by the product
+library.  It shares no
 code with the CUDA path.  The arithmetic lives in ``amc_oracle.c`` (plain C,
 double precision, written step by step after the paper); this module only
 marshals numpy arrays into it and reads the raw Joe-Kuo data (primitive
@@ -21,6 +22,17 @@ Functions and the passages they follow:
   bs             Black-Scholes, Eqs. 1-5
   crr            Cox-Ross-Rubinstein tree (Bermudan or American)
   pathwise_greeks frozen-boundary pathwise delta and vega
+  solve_normal   equilibrated Cholesky solve of one date's normal equations
+  price, greeks  the above from option parameters (points, paths, rule)
+  lcg_params, lcg_perm, paths_permuted
+                 the paper's LCG-permuted points (§III.D)
+  value_boundary, price_oos
+                 a fitted boundary applied to other paths (second pass,
+                 ref. [12])
+  dual_normal, dual_upper, price_dual
+                 Andersen-Broadie dual upper bound of a fitted boundary
+                 (§IV, ref. [11])
+  bridge_matrix  the bridge as a linear map W = A z (for the covariance pin)
 """
 import ctypes
 import os

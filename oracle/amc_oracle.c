@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
  * executes this file; only the test-suite, the smoke check and the CPU
- * baseline leg of the benchmark load it.  It shares no code, header, table
+ * baseline leg and reference arm of the benchmark load it.  It shares no code, header, table
  * or constant generator with the CUDA path: the Sobol direction numbers are
  * expanded here from the raw Joe-Kuo (polynomial, initial numbers) data by
  * this file's own recurrence, the inverse normal is the root of Phi(z) = u
