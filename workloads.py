@@ -7,9 +7,9 @@ from numpy's PCG64 generator with a fixed seed.
 
 Workloads:
   single_small   one American put, S0=36, K=40, r=0.06, sigma=0.2, T=1,
-                 50 dates, 2^14 paths, basis {1,x,x^2}, shift seed 1
+                 50 dates, 2^14 paths, basis size 3, shift seed 1
   single_large   one American put, S0=100, K=100, r=0.05, sigma=0.3, T=1,
-                 252 dates, 2^20 paths, basis {1,x,x^2,x^3}, shift seed 2
+                 252 dates, 2^20 paths, basis size 4, shift seed 2
   batch_options  4096 puts/calls, seed 3: S0, K ~ U[80,120],
                  sigma ~ U[0.1,0.5], r ~ U[0,0.08], T ~ U[0.25,2],
                  n_steps ~ U{12..365}, n_paths = 2^k with k ~ U{14..18},
@@ -18,6 +18,10 @@ Workloads:
                  parameters drawn as in batch_options
   greeks_options 1024 puts, seed 5, drawn as batch_options but with
                  2^18 paths and 100 dates
+  fig1_options   the Longstaff-Schwartz Table 1 put on nested power-of-two
+                 date grids, one shift seed, for LSM and the paper's rule
+A basis of size p spans {1, S, .., S^(p-1)}; the library and the oracle
+regress on powers of the moneyness y = S/K - 1, the same span.
 """
 from dataclasses import asdict, dataclass
 
