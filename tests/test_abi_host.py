@@ -134,3 +134,29 @@ def test_library_lcg_permutation_parameters(amc, n):
     np.testing.assert_array_equal(c.astype(np.uint64), co)
     if M >= 4:
         assert np.all(a % 4 == 1) and np.all(c % 2 == 1)
+
+
+def test_host_helpers_reject_bad_arguments(amc):
+    """Every host-only helper returns AMC_EINVAL for arguments outside its
+    documented range, and the size helpers return 0 for empty inputs."""
+    def einval(fn, *args):
+        with pytest.raises(amc.AmcError) as ei:
+            fn(*args)
+        assert ei.value.code == amc.AMC_EINVAL, (fn.__name__, args)
+
+    for m in (0, amc.AMC_MAX_STEPS + 1):
+        einval(amc.amc_sobol_directions, m)
+        einval(amc.amc_bridge_schedule, m)
+    assert amc.amc_sobol_directions(amc.AMC_MAX_STEPS).shape == (amc.AMC_MAX_STEPS, 32)
+    assert sorted(amc.amc_bridge_schedule(amc.AMC_MAX_STEPS)[0].tolist()) == list(range(1, amc.AMC_MAX_STEPS + 1))
+    assert amc.lib().amc_digital_shifts(1, -1, None) == amc.AMC_EINVAL      # below the binding's numpy sizing
+    assert amc.amc_digital_shifts(1, 0).shape == (0,)
+    for n_dims, n_points in ((0, 10), (amc.AMC_MAX_STEPS + 1, 10), (3, 0), (3, 2 ** 31 + 1)):
+        einval(amc.amc_lcg_params, 5, n_dims, n_points)
+    for n_paths, sms in ((0, 152), (-1, 152), (1000, 0)):
+        einval(amc.amc_plan_sweep, n_paths, sms)
+    assert amc.amc_path_ld(0) == 0 and amc.amc_path_ld(-3) == 0
+    assert amc.amc_path_bytes(0, 100, amc.AMC_MIXED) == 0 and amc.amc_path_bytes(10, 0, amc.AMC_FP64) == 0
+    for code in (amc.AMC_EINVAL, amc.AMC_ENOMEM, amc.AMC_ECUDA, amc.AMC_EBUSY, amc.AMC_PENDING, amc.AMC_ENOTFOUND):
+        assert amc.strerror(code) and amc.strerror(code) != amc.strerror(0)
+    assert amc.strerror(-12345)                                     # unknown codes still get a string
