@@ -576,3 +576,43 @@ def test_oracle_results_do_not_depend_on_its_thread_count():
     assert np.array_equal(S, S1)
     assert fit["price"] == fit1["price"] and np.array_equal(fit["beta"], fit1["beta"])
     assert d == d1
+
+
+def test_standard_errors_are_the_sample_deviation_of_the_discounted_path_values():
+    """Every estimator's std_err is the sample standard deviation (N - 1) of
+    the per-path values discounted to t = 0, over sqrt(N), and its price is
+    their mean (Eqs. 6-8): recomputed in numpy from the paths, the stopping
+    dates and the per-path values, for LSM, its out-of-sample valuation, the
+    European estimator, the paper's rule and the dual bound."""
+    S0, K, r, sigma, T, m, N = 36.0, 40.0, .06, .2, 1.0, 9, 3000
+    dt = T / m
+    S = oracle.paths(S0, r, sigma, T, m, N, seed=9)
+    idx = np.arange(N)
+
+    def check(res, v, key="price"):
+        assert abs(res[key] - v.mean()) < 1e-12 * max(1.0, abs(v.mean()))
+        assert abs(res["std_err"] - v.std(ddof=1) / math.sqrt(N)) < 1e-12 * v.std()
+
+    fit = oracle.lsm(S, oracle.PUT, K, r, T, 3, details=True)
+    tau = fit["tau"].astype(np.int64)
+    assert tau.min() >= 1 and tau.max() <= m
+    check(fit, np.exp(-r * tau * dt) * np.maximum(K - S[tau - 1, idx], 0.0))
+
+    S2 = oracle.paths(S0, r, sigma, T, m, N, seed=10)
+    val = oracle.value_boundary(S2, oracle.PUT, K, r, T, fit["beta"], fit["deg"], details=True)
+    t2 = val["tau"].astype(np.int64)
+    check(val, np.exp(-r * t2 * dt) * np.maximum(K - S2[t2 - 1, idx], 0.0))
+
+    check(oracle.european(S, oracle.CALL, K, r, T), np.exp(-r * T) * np.maximum(S[-1] - K, 0.0))
+
+    full = np.vstack([np.full((1, N), S0), S])
+    h = np.maximum(K - full, 0.0)
+    last = np.maximum(h[m - 1], [oracle.bs(oracle.PUT, s, K, r, sigma, dt) for s in full[m - 1]])
+    V = np.max([np.exp(-r * j * dt) * h[j] for j in range(m - 1)] + [np.exp(-r * (m - 1) * dt) * last], axis=0)
+    check(oracle.paper_ub(S, oracle.PUT, S0, K, r, sigma, T), V)
+
+    So = oracle.paths(S0, r, sigma, T, m, 200, seed=11)
+    up = oracle.dual_upper(So, oracle.PUT, K, r, sigma, T, fit["beta"], fit["deg"], 8, 5, details=True)
+    U = up["U"]
+    assert abs(up["upper"] - U.mean()) < 1e-12 * U.mean()
+    assert abs(up["std_err"] - U.std(ddof=1) / math.sqrt(len(U))) < 1e-12 * U.std()
