@@ -616,3 +616,21 @@ def test_standard_errors_are_the_sample_deviation_of_the_discounted_path_values(
     U = up["U"]
     assert abs(up["upper"] - U.mean()) < 1e-12 * U.mean()
     assert abs(up["std_err"] - U.std(ddof=1) / math.sqrt(len(U))) < 1e-12 * U.std()
+
+
+def test_too_few_in_the_money_paths_make_a_degenerate_date():
+    """Reading of the degenerate-date rule: fewer than p paths strictly in
+    the money at a date (a path at the strike is not) means no regression
+    and no exercise there, counted once; with p at most that count the date
+    is regressed.  Hand-made put paths, K = 1, 3 dates, 7 paths."""
+    K, r, T = 1.0, 0.05, 3.0
+    S = np.array([[0.50, 0.60, 0.70, 0.80, 1.20, 1.30, 1.40],     # date 1: 4 in the money
+                  [0.10, 0.20, 1.00, 1.10, 1.20, 1.30, 1.40],     # date 2: 2 in the money (1.00 is at the strike)
+                  [0.90, 0.95, 1.10, 0.97, 1.20, 0.99, 1.40]])    # maturity
+    deep = oracle.lsm(S, oracle.PUT, K, r, T, 3, details=True)
+    assert deep["n_itm"].tolist()[:2] == [4, 2]
+    assert deep["deg"].tolist()[1] == 1 and deep["degenerate_dates"] == 1
+    assert 2 not in deep["tau"].tolist()                           # deep in the money at date 2, yet never exercised
+    two = oracle.lsm(S, oracle.PUT, K, r, T, 2, details=True)
+    assert two["deg"].tolist()[1] == 0 and two["degenerate_dates"] == 0
+    assert two["tau"].tolist()[:2] == [2, 2]                        # exact fit through the 2 points: exercise
