@@ -634,3 +634,21 @@ def test_too_few_in_the_money_paths_make_a_degenerate_date():
     two = oracle.lsm(S, oracle.PUT, K, r, T, 2, details=True)
     assert two["deg"].tolist()[1] == 0 and two["degenerate_dates"] == 0
     assert two["tau"].tolist()[:2] == [2, 2]                        # exact fit through the 2 points: exercise
+
+
+def test_exercise_and_moneyness_tests_are_strict():
+    """Reading of the tie-breaks: a path exercises only where its payoff
+    strictly exceeds the continuation value, and only strictly in the money.
+    A constant boundary (p = 1) of 0.25 K at date 1 and exact binary values:
+    payoff 0.25 equals it (kept), 0.5 exceeds it (exercised); a path at the
+    strike with a boundary below zero is not in the money (kept)."""
+    K, r, T = 1.0, 0.0, 2.0
+    S = np.array([[0.75, 0.50, 1.00],
+                  [1.50, 1.50, 1.50]])                               # maturity: out of the money
+    beta = np.array([[0.25], [0.0]])
+    deg = np.array([0, 1], dtype=np.int32)
+    res = oracle.value_boundary(S, oracle.PUT, K, r, T, beta, deg, details=True)
+    assert res["tau"].tolist() == [2, 1, 2]
+    assert res["price"] == 0.5 / 3
+    below = oracle.value_boundary(S, oracle.PUT, K, r, T, np.array([[-1.0], [0.0]]), deg, details=True)
+    assert below["tau"].tolist() == [1, 1, 2]                        # S = K is not exercised even against c < 0
