@@ -652,3 +652,26 @@ def test_exercise_and_moneyness_tests_are_strict():
     assert res["price"] == 0.5 / 3
     below = oracle.value_boundary(S, oracle.PUT, K, r, T, np.array([[-1.0], [0.0]]), deg, details=True)
     assert below["tau"].tolist() == [1, 1, 2]                        # S = K is not exercised even against c < 0
+
+
+@pytest.mark.parametrize("m", [13, 16])
+def test_shifted_paths_rebuilt_from_scipy_points(m):
+    """Steps 1-3 end to end: path i is the GBM (Eq. 9 in log space) of the
+    bridge of ndtri((x + 1/2) 2^-32) of scipy's Sobol' point i (point 0
+    included) XOR the digital shift of each dimension; a block starting at
+    `first` is the same columns of the whole array."""
+    from scipy.stats import qmc
+    from scipy.special import ndtri
+    N, seed, S0, r, sig, T = 600, 12, 100.0, .05, .3, 1.5
+    S, W = oracle.paths(S0, r, sig, T, m, N, seed, with_W=True)
+    pts = qmc.Sobol(d=m, scramble=False, bits=32).random(1024)
+    X = np.round(pts * 2.0 ** 32).astype(np.uint64) ^ oracle.shifts(seed, m).astype(np.uint64)[None, :]
+    A = oracle.bridge_matrix(m, T)
+    t = np.arange(1, m + 1) * (T / m)
+    for i in (0, 1, 2, 511, 599):
+        u = (X[i].astype(np.float64) + 0.5) / 2.0 ** 32
+        Wi = A @ ndtri(u)
+        np.testing.assert_allclose(W[:, i], Wi, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(S[:, i], S0 * np.exp((r - 0.5 * sig * sig) * t + sig * Wi), rtol=1e-12)
+    part = oracle.paths(S0, r, sig, T, m, 100, seed, first=450)
+    np.testing.assert_array_equal(part, S[:, 450:550])
