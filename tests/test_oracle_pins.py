@@ -109,6 +109,19 @@ def test_bridge_schedule_visits_every_date_once(m):
         seen.add(int(date[k]))
 
 
+@pytest.mark.parametrize("m,date,left,right", [
+    (5, [5, 2, 1, 3, 4], [0, 0, 0, 2, 3], [0, 5, 2, 5, 5]),
+    (7, [7, 3, 1, 5, 2, 4, 6], [0, 0, 0, 3, 1, 3, 5], [0, 7, 3, 7, 3, 5, 7]),
+])
+def test_bridge_schedule_worked_examples(m, date, left, right):
+    """The bridge reading worked out by hand for dates that are not a power
+    of two: W(t_m) first, then the intervals (l, r) split breadth-first, left
+    before right, at floor((l + r) / 2), each node conditioned on the ends of
+    its interval."""
+    d, l, r = oracle.bridge_schedule(m)
+    assert (d.tolist(), l.tolist(), r.tolist()) == (date, left, right)
+
+
 def test_bridge_power_of_two_is_textbook_bisection():
     m = 16
     date, _, _ = oracle.bridge_schedule(m)
