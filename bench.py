@@ -888,7 +888,8 @@ def run_amc(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # 300 steps of the 1.4 ms bench pricing: a 0.4 s timed region, several clock samples at 100 ms
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["amc", "reference"], default="amc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
