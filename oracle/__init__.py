@@ -93,7 +93,8 @@ def _lib():
         lib.orc_lsm.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp, _i32p, _dp, _i64p, _i32p]
         lib.orc_value_boundary.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _i32p, _dp, _i32p]
+                                           ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _i32p, _dp, _i32p,
+                                           _dp]
         lib.orc_paper_ub.argtypes = [ctypes.c_int] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
         lib.orc_european.argtypes = [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_int64, _dp, _dp]
         lib.orc_pathwise_greeks.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 5 +
@@ -265,10 +266,13 @@ def lsm(S, type_, K, r, T, p, details=False):
     return res
 
 
-def value_boundary(S, type_, K, r, T, beta, deg, details=False):
+def value_boundary(S, type_, K, r, T, beta, deg, details=False, cf_dates=False):
     """Value the paths S with a given exercise boundary: beta[m, p] in
     currency units on the basis (1, y, .., y^(p-1)), y = S/K - 1; deg[m]
-    nonzero = no exercise at that date."""
+    nonzero = no exercise at that date.  cf_dates: also return "cf_dates"
+    [m, N], the cash flow of each path under the boundary discounted to t_j
+    before the decision at t_j (row j-1), which is what the regression of
+    date j is fitted to when the later decisions are the boundary's."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     deg = np.ascontiguousarray(deg, dtype=np.int32)
@@ -276,13 +280,16 @@ def value_boundary(S, type_, K, r, T, beta, deg, details=False):
     p = beta.shape[1]
     out = np.zeros(3)
     tau = np.zeros(N, dtype=np.int32) if details else None
+    cfd = np.zeros((m, N)) if cf_dates else None
     rc = _lib().orc_value_boundary(type_, K, r, T, m, N, p, _ptr(S, _dp), _ptr(beta, _dp), _ptr(deg, _i32p),
-                                   _ptr(out, _dp), _ptr(tau, _i32p))
+                                   _ptr(out, _dp), _ptr(tau, _i32p), _ptr(cfd, _dp))
     if rc != 0:
         raise ValueError("oracle value_boundary failed")
     res = {"price": out[0], "std_err": out[1], "degenerate_dates": int(out[2])}
     if details:
         res["tau"] = tau
+    if cf_dates:
+        res["cf_dates"] = cfd
     return res
 
 

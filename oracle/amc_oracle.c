@@ -533,9 +533,13 @@ int orc_lsm(int type, double K, double r, double T, int m, int64_t N, int p,
  *   price = e^{-r dt} mean(CF),  std_err = e^{-r dt} sd(CF) / sqrt(N).
  * With the coefficients fitted on these same paths it repeats the in-sample
  * decisions; on paths independent of the fit it is a low-biased estimator
- * of the Bermudan value (any stopping rule is at most optimal).           */
+ * of the Bermudan value (any stopping rule is at most optimal).
+ * Optional cf_out[(j-1)*N + i], j = 1..m: the cash flow of path i under this
+ * boundary discounted to t_j, before the decision at t_j (for j = m, h(S_m)):
+ * what the least-squares regression of date j (ref. [12]) is fitted to when
+ * the decisions at the later dates are this boundary's.                    */
 int orc_value_boundary(int type, double K, double r, double T, int m, int64_t N, int p, const double *S,
-                       const double *beta, const int32_t *deg, double *out, int32_t *tau_out)
+                       const double *beta, const int32_t *deg, double *out, int32_t *tau_out, double *cf_out)
 {
     double dt = T / m, disc = exp(-r * dt);
     double *CF = (double *)malloc(sizeof(double) * (size_t)N);
@@ -546,8 +550,10 @@ int orc_value_boundary(int type, double K, double r, double T, int m, int64_t N,
     for (int64_t i = 0; i < N; ++i) {
         double cf = orc_payoff(type, S[(int64_t)(m - 1) * N + i], K);
         int32_t tau = m;
+        if (cf_out) cf_out[(int64_t)(m - 1) * N + i] = cf;
         for (int j = m - 1; j >= 1; --j) {
             cf *= disc;
+            if (cf_out) cf_out[(int64_t)(j - 1) * N + i] = cf;
             if (deg[j - 1]) continue;
             double s = S[(int64_t)(j - 1) * N + i];
             double h = orc_payoff(type, s, K);

@@ -42,3 +42,34 @@ def lsm_micro(S, type_, K, r, T, p, center=1.0):
         cf[ex] = h[ex]
         tau[ex] = j
     return {"price": disc * cf.mean(), "beta": beta, "tau": tau, "cf": cf, "degenerate_dates": degenerate}
+
+
+def cash_flows_under_boundary(S, type_, K, r, T, beta, deg):
+    """Brute force, one path and one date at a time: the cash flow of each
+    path under a given exercise boundary (beta[m, p] in currency units on the
+    basis 1, y, .., y^(p-1), y = S/K - 1; deg[m] nonzero = no exercise),
+    discounted to t_j before the decision at t_j.  Returns cf[m, N]; row j-1
+    is what the regression of date j is fitted to when the later decisions
+    are the boundary's (ref. [12])."""
+    S = np.asarray(S, dtype=np.float64)
+    m, N = S.shape
+    disc = np.exp(-r * T / m)
+    out = np.zeros((m, N))
+    for i in range(N):
+        s_m = S[m - 1, i]
+        c = max(s_m - K, 0.0) if type_ == 1 else max(K - s_m, 0.0)
+        out[m - 1, i] = c
+        for j in range(m - 1, 0, -1):
+            c = c * disc
+            out[j - 1, i] = c
+            if deg[j - 1]:
+                continue
+            s = S[j - 1, i]
+            h = max(s - K, 0.0) if type_ == 1 else max(K - s, 0.0)
+            if not h > 0.0:
+                continue
+            y = s / K - 1.0
+            cont = sum(beta[j - 1][k] * y ** k for k in range(len(beta[j - 1])))
+            if h > cont:
+                c = h
+    return out

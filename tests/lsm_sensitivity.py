@@ -66,16 +66,20 @@ def fp32_sum_shift(o):
     return abs(lsm_fp32_sums(S, o) - ref)
 
 
-def check_mixed_vs_oracle(o, got, ref, fp64_price, bar=2e-4):
+def check_mixed_vs_oracle(o, got, ref, fp64_price, replay, bar=2e-4):
     """A mixed-precision price `got` against the oracle's `ref` on the same
-    points: within bar K; or, where the oracle's own price moves by more than
-    half the bar under FP32-level path noise or FP32 sums (LSM unstable at
-    FP32 precision on this option), within three times that movement, and
-    the FP64 GPU price (fp64_price(), called only then) within bar K."""
+    points: within bar K.  Otherwise the option must be one on which the LSM
+    estimator is unstable at FP32 precision (the oracle's own price moves by
+    more than half the bar under FP32-level path noise or FP32 sums), and
+    then the kernel is held to its arithmetic instead: replay() runs the
+    replay check of the mixed sweep on its own FP32 paths (every date's
+    normal equations and the price within their FP32 bounds,
+    tests/lsm_replay.py), and the FP64 GPU price fp64_price() must be within
+    bar K of the oracle."""
     err = abs(got - ref) / o.K
     if err <= bar:
         return
     spread = max(path_noise_spread(o, reps=2), fp32_sum_shift(o))
     assert spread > bar / 2, ("mixed price off the oracle on an FP32-stable option", o, got, ref, spread)
-    assert err <= 3 * spread, (o, got, ref, spread)
+    replay()
     assert abs(fp64_price() - ref) <= bar * o.K, (o, ref)

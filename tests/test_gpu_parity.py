@@ -20,6 +20,7 @@ import pytest
 
 import oracle
 import workloads
+from lsm_replay import gpu_fit, gpu_replay, replay_check
 from lsm_sensitivity import check_mixed_vs_oracle
 
 pytestmark = pytest.mark.gpu
@@ -155,30 +156,45 @@ PRICE_CASES = [
 # LSM with a cubic over a very wide moneyness range is unstable at FP32
 # precision: the oracle's own price moves by more than 2e-4 K under path noise
 # at the FP32 paths' error level, and (volatility 150 %) under FP32 sums on
-# identical paths (tests/test_fp32_sensitivity.py).  These two cases keep the
-# 2e-4 K bar in FP64; in mixed precision no FP32 implementation can hold it.
+# identical paths (tests/test_fp32_sensitivity.py).  On these two cases the
+# mixed price is held to the replay check instead (tests/lsm_replay.py: every
+# date's normal equations and the price within the FP32 bounds of the
+# kernel's own arithmetic on its own paths) and the FP64 price to 2e-4 K.
 UNSTABLE_IN_FP32 = {"huge_vol", "long_call"}
 
 
 @pytest.mark.parametrize("name,opt", PRICE_CASES, ids=[c[0] for c in PRICE_CASES])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
 def test_price_vs_oracle(amc, ctx, name, opt, prec):
-    if prec == 1 and name in UNSTABLE_IN_FP32 and opt.rule == 0:
-        pytest.skip("LSM estimator unstable at FP32 precision (tests/test_fp32_sensitivity.py)")
     ref = _oracle_price(opt)
     got = _gpu_price(amc, ctx, opt, prec)
     assert got["status"] == 0
-    assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+    if prec == 1 and name in UNSTABLE_IN_FP32 and opt.rule == 0:
+        check_mixed_vs_oracle(opt, got["price"], ref["price"], lambda: _gpu_price(amc, ctx, opt, 0)["price"],
+                              lambda: gpu_replay(amc, ctx, opt))
+    else:
+        assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
     assert got["degenerate_dates"] == ref["degenerate_dates"]
     assert abs(got["std_err"] - ref["std_err"]) <= 1e-3 * max(ref["std_err"], 1e-12) + 2e-4 * opt.K
 
 
 @pytest.mark.parametrize("name,opt", PRICE_CASES, ids=[c[0] for c in PRICE_CASES])
 def test_mixed_sweep_on_identical_paths(amc, ctx, torch, name, opt):
-    """The mixed sweep alone: the oracle's FP64 sweep run on the GPU's own
-    FP32 paths, so only the sweep arithmetic differs."""
-    if name in UNSTABLE_IN_FP32 and opt.rule == 0:
-        pytest.skip("LSM estimator unstable at FP32 precision (tests/test_fp32_sensitivity.py)")
+    """The mixed sweep alone, on the GPU's own FP32 paths.  LSM: the replay
+    check (tests/lsm_replay.py) holds every date's regression and the price
+    to the FP32 bounds of the kernel's arithmetic given its own decisions;
+    on the options where the estimator is stable at FP32 precision the
+    price is also within 2e-4 K of the oracle's free-running FP64 sweep on
+    the same paths.  The other rules: the oracle on the same paths."""
+    Sh, coef, got = gpu_fit(amc, ctx, torch, opt) if opt.rule == 0 else (None, None, None)
+    if opt.rule == 0:
+        d = replay_check(Sh, opt, coef, got)
+        assert d["residual_ratio"] <= 1.0
+        ref = oracle.lsm(Sh, opt.type, opt.K, opt.r, opt.T, opt.basis)
+        if name not in UNSTABLE_IN_FP32:
+            assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+        assert got["degenerate_dates"] == ref["degenerate_dates"]
+        return
     ld = amc.amc_path_ld(opt.n_paths)
     S = torch.empty((opt.n_steps, ld), dtype=torch.float32, device="cuda")
     res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
@@ -187,9 +203,7 @@ def test_mixed_sweep_on_identical_paths(amc, ctx, torch, name, opt):
     torch.cuda.synchronize()
     got = amc.res_to_dict(res.cpu().numpy())
     Sh = S[:, :opt.n_paths].double().cpu().numpy()
-    if opt.rule == 0:
-        ref = oracle.lsm(Sh, opt.type, opt.K, opt.r, opt.T, opt.basis)
-    elif opt.rule == 1:
+    if opt.rule == 1:
         ref = oracle.paper_ub(Sh, opt.type, opt.S0, opt.K, opt.r, opt.sigma, opt.T)
     else:
         ref = oracle.european(Sh, opt.type, opt.K, opt.r, opt.T)
@@ -232,18 +246,38 @@ def test_full_batch_sampled_vs_oracle_and_alone(amc, ctx):
     oracle on the same points, with equal degenerate counts.  Options on
     which LSM is unstable at FP32 precision (deep in-the-money calls with a
     wide moneyness range) are held to the oracle's own FP32 sensitivity, and
-    their FP64 GPU price to 2e-4 K (check_mixed_vs_oracle)."""
+    their FP64 GPU price to 2e-4 K, while the mixed sweep is held to the
+    replay check on its own paths, priced alone, whose result equals the
+    batch's bit for bit (check_mixed_vs_oracle)."""
     opts = workloads.batch_options()
     res = amc.amc_price_batch(ctx, opts, amc.AMC_MIXED)
     assert all(r["status"] == 0 for r in res)
     for i in np.random.default_rng(43).choice(len(opts), size=16, replace=False):
         s = _gpu_price(amc, ctx, opts[i], amc.AMC_MIXED)
         assert res[i]["price"] == s["price"] and res[i]["std_err"] == s["std_err"], (i, res[i], s)
+
+    def replay_alone(i):
+        s = _gpu_price(amc, ctx, opts[i], amc.AMC_MIXED)
+        assert res[i]["price"] == s["price"], (i, res[i], s)
+        gpu_replay(amc, ctx, opts[i])
+
     for i in np.random.default_rng(44).choice(len(opts), size=len(opts) // 100, replace=False):
         o = opts[i]
         ref = _oracle_price(o)
-        check_mixed_vs_oracle(o, res[i]["price"], ref["price"], lambda: _gpu_price(amc, ctx, o, amc.AMC_FP64)["price"])
+        check_mixed_vs_oracle(o, res[i]["price"], ref["price"], lambda: _gpu_price(amc, ctx, o, amc.AMC_FP64)["price"],
+                              lambda: replay_alone(i))
         assert res[i]["degenerate_dates"] == ref["degenerate_dates"]
+
+
+def test_batch_option_659_replay(amc, ctx):
+    """Batch option 659, a deep in-the-money call with a wide moneyness range
+    on which LSM is unstable at FP32 precision: the replay check on its own
+    paths, and the batch result equal to the option priced alone."""
+    o = workloads.batch_options()[659]
+    d = gpu_replay(amc, ctx, o)
+    assert d["residual_ratio"] <= 1.0 and d["price_ratio"] <= 1.0
+    b = amc.amc_price_batch(ctx, [o], amc.AMC_MIXED)[0]
+    assert b["price"] == _gpu_price(amc, ctx, o, amc.AMC_MIXED)["price"]
 
 
 def test_full_greeks_sampled_vs_oracle(amc, ctx):
@@ -257,7 +291,8 @@ def test_full_greeks_sampled_vs_oracle(amc, ctx):
         g = oracle.greeks(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
                           seed=o.seed, rule=o.rule)
         if abs(p[i] - g["price"]) > 2e-4 * o.K:      # unstable at FP32 precision: FP64 Greeks carry the bars
-            check_mixed_vs_oracle(o, p[i], g["price"], lambda: amc.amc_greeks(ctx, [o], amc.AMC_FP64)[0][0])
+            check_mixed_vs_oracle(o, p[i], g["price"], lambda: amc.amc_greeks(ctx, [o], amc.AMC_FP64)[0][0],
+                                  lambda: gpu_replay(amc, ctx, o))
             _, dd, vv = amc.amc_greeks(ctx, [o], amc.AMC_FP64)
             assert abs(dd[0] - g["delta"]) <= 1e-9 + 5e-4 and abs(vv[0] - g["vega"]) <= 0.1, (i, dd, vv, g)
             continue

@@ -93,12 +93,13 @@ def test_served_stream_vs_alone_fp64_and_oracle(amc):
     precision: every served result equals the request priced alone, bit for
     bit; a seeded 5 % sample is within 2e-4 K of the all-FP64 GPU path and a
     seeded 1 % sample within 2e-4 K of the FP64 oracle on the same points,
-    except where LSM is unstable at FP32 precision on the request, which is
-    then held to the oracle's own FP32 sensitivity and its FP64 GPU price
-    to 2e-4 K (check_mixed_vs_oracle)."""
+    except where LSM is unstable at FP32 precision on the request, whose
+    mixed sweep is then held to the replay check on its own paths and its
+    FP64 GPU price to 2e-4 K (check_mixed_vs_oracle)."""
     import numpy as np
 
     import oracle
+    from lsm_replay import gpu_replay
     from lsm_sensitivity import check_mixed_vs_oracle
     _, opts = workloads.serving_requests(rate=2000.0, duration=1.0, seed=4)
     with amc.Context(0, arena_bytes=24 << 30) as ctx:
@@ -128,12 +129,14 @@ def test_served_stream_vs_alone_fp64_and_oracle(amc):
         if abs(got[i]["price"] - f) > 2e-4 * o.K:    # only where LSM is unstable at FP32 precision
             ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
                                seed=o.seed, rule=o.rule)
-            check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: f)
+            with amc.Context(0, arena_bytes=2 << 30) as c2:
+                check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: f, lambda: gpu_replay(amc, c2, o))
     for i in sample:
         o = opts[i]
         ref = oracle.price(o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, basis=o.basis, type=o.type,
                            seed=o.seed, rule=o.rule)
-        check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: fp64[i])
+        with amc.Context(0, arena_bytes=2 << 30) as c2:
+            check_mixed_vs_oracle(o, got[i]["price"], ref["price"], lambda: fp64[i], lambda: gpu_replay(amc, c2, o))
         assert got[i]["degenerate_dates"] == ref["degenerate_dates"]
 
 

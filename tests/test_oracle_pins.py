@@ -363,6 +363,51 @@ def test_boundary_valuation_on_fitting_paths_repeats_in_sample_decisions():
     assert val["degenerate_dates"] == fit["degenerate_dates"]
 
 
+def test_cash_flows_under_a_boundary_match_brute_force():
+    """The per-date cash flows of the boundary valuation (what the
+    regression of each date is fitted to under that boundary) against a
+    pure-Python loop over paths and dates (oracle/micro.py), entry by entry,
+    for a put and a call, with a degenerate date, an ITM-everywhere boundary
+    and the fitted one."""
+    from oracle.micro import cash_flows_under_boundary
+    for tp, S0, K, seed in ((oracle.PUT, 36.0, 40.0, 5), (oracle.CALL, 44.0, 40.0, 6)):
+        m, n, r, T = 7, 40, .06, 1.0
+        S = oracle.paths(S0, r, .3, T, m, n, seed)
+        fit = oracle.lsm(S, tp, K, r, T, 3, details=True)
+        rng = np.random.default_rng(seed)
+        for beta, deg in ((fit["beta"], fit["deg"]),
+                          (rng.normal(0.0, 2.0, (m, 3)), (np.arange(m) == 3).astype(np.int32)),
+                          (np.full((m, 2), -1e300), np.zeros(m, dtype=np.int32))):
+            got = oracle.value_boundary(S, tp, K, r, T, beta, deg, cf_dates=True)["cf_dates"]
+            ref = cash_flows_under_boundary(S, tp, K, r, T, beta, deg)
+            np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-14)
+
+
+def test_regressions_on_the_cash_flows_under_the_fitted_boundary_reproduce_it():
+    """Regressing each date's cash flows under the oracle's own fitted
+    boundary (in-the-money paths, the oracle's normal equations) gives back
+    the coefficients the LSM sweep fitted at that date: the cash flows are
+    exactly the ones the sweep regressed on."""
+    for tp, S0, p, seed in ((oracle.PUT, 36.0, 3, 7), (oracle.CALL, 44.0, 4, 8)):
+        m, K, r, T = 30, 40.0, .06, 1.0
+        S = oracle.paths(S0, r, .25, T, m, 4096, seed)
+        fit = oracle.lsm(S, tp, K, r, T, p, details=True)
+        cfd = oracle.value_boundary(S, tp, K, r, T, fit["beta"], fit["deg"], cf_dates=True)["cf_dates"]
+        checked = 0
+        for j in range(1, m):
+            if fit["deg"][j - 1]:
+                continue
+            h = np.maximum(S[j - 1] - K, 0.0) if tp == oracle.CALL else np.maximum(K - S[j - 1], 0.0)
+            I = h > 0
+            y = S[j - 1][I] / K - 1.0
+            X = np.vander(y, p, increasing=True)
+            beta = oracle.solve_normal(X.T @ X, X.T @ cfd[j - 1][I])
+            fitted, ref = X @ beta, X @ fit["beta"][j - 1]
+            assert np.max(np.abs(fitted - ref)) <= 1e-9 * K, (j, np.max(np.abs(fitted - ref)))
+            checked += 1
+        assert checked >= m // 2
+
+
 def test_boundary_without_exercise_is_the_european_estimator():
     S, fit = _fit(2)
     m = S.shape[0]
