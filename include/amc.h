@@ -123,6 +123,13 @@ int amc_ctx_set_timeout(amc_ctx *ctx, double seconds);
  *           (cash flows in device memory, one pass and one solve per date)
  *           whatever its path count, so that it can be tested on small
  *           options;
+ *   kind 4: the next mixed-precision LSM launch of amc_price_batch,
+ *           amc_greeks, their _device forms or the serving loop takes the
+ *           launch tag `arg` (1 <= arg < 2^22) of its cross-CTA exchange
+ *           units instead of a new one, so that units an earlier launch
+ *           left in the same arena memory carry the tag the new launch
+ *           waits for: a test that stale exchange data is never taken for
+ *           fresh (results must not change);
  *   kind 0: clear.                                                          */
 int amc_ctx_inject(amc_ctx *ctx, int kind, int64_t arg);
 /* Bytes of the arena currently free / total.                               */
@@ -258,20 +265,42 @@ int amc_dual_upper(amc_ctx *ctx, const amc_option *opt, int prec, const void *S_
                    double *U_dev, void *stream);
 
 /* --------------------------------------------------- host-level calls */
-/* Price one option (paths in the context arena), blocking; out on host.   */
+/* Price one option (paths in the context arena), blocking; out on host.
+ * The paper's problem statement: one option valued on a large number of
+ * quasi-random paths (§III.D), inputs S0, K, T, r, sigma (Eqs. 1-5, §V),
+ * m exercise dates t_j = j T/m (§III.E, §V), the early-exercise rule by
+ * backward induction (§V; LSM, ref. [12], or Eqs. 10-11) and the average
+ * of Eq. 6 discounted to t = 0 (Eqs. 7-8).                                 */
 int amc_price_american(amc_ctx *ctx, double S0, double K, double r, double sigma,
                        double T, int n_steps, int64_t n_paths, int basis, int type,
                        uint64_t seed, int rule, int prec, amc_result *out);
-/* Price n options; each option's result equals its amc_price_american
- * result bit for bit.  Options are grouped into arena-sized waves; within a
- * wave path generation runs as one launch and the sweeps as one persistent
- * launch.  Blocking; out[n] on host.                                       */
+/* Price n options (the many-options setting that motivates the paper's GPU
+ * design, §III.D and §VI); each option's result equals its
+ * amc_price_american result bit for bit.  Options are grouped into
+ * arena-sized waves; within a wave path generation runs as one launch and
+ * the sweeps as one persistent launch, each option on its own CTA group.
+ * Blocking; out[n] on host.                                                */
 int amc_price_batch(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                     amc_result *out);
+/* amc_price_batch on a caller's stream with the results on the device: the
+ * result block of option i (AMC_RES_DOUBLES doubles, [price, std_err, 0, 0,
+ * degenerate_dates, status, 0, 0]) into res_dev[i * AMC_RES_DOUBLES]
+ * (device memory, 8-byte aligned, caller-owned; n * AMC_RES_DOUBLES
+ * doubles).  The work is ordered after everything already queued on
+ * `stream` and later work on `stream` is ordered after it; the call returns
+ * without waiting for the GPU.  Results equal amc_price_batch's bit for bit.
+ * Validation errors (AMC_EINVAL) are returned before any device work; a
+ * per-option failure (e.g. AMC_ETIMEOUT) is that option's status in
+ * res_dev; on any other nonzero return the contents of res_dev are
+ * unspecified.  The context's arena is in use until the work has finished:
+ * the next call on the context is ordered after it on the GPU.            */
+int amc_price_batch_device(amc_ctx *ctx, const amc_option *opts, int n, int prec,
+                           double *res_dev, void *stream);
 /* Out-of-sample LSM price (paths in the context arena), blocking: the
  * boundary is fitted on the points of opt->seed (in-sample result into
  * fit, may be null) and applied to the independent points of value_seed
- * (result into value).                                                     */
+ * (result into value).  The second Longstaff-Schwartz pass of ref. [12];
+ * the paper prices in sample (§V).                                         */
 int amc_price_oos(amc_ctx *ctx, const amc_option *opt, uint64_t value_seed, int prec,
                   amc_result *fit, amc_result *value);
 /* Lower and upper bounds of the Bermudan value, blocking: the boundary is
@@ -279,12 +308,33 @@ int amc_price_oos(amc_ctx *ctx, const amc_option *opt, uint64_t value_seed, int 
  * null); on n_outer independent paths of outer_seed it is applied
  * (amc_value_boundary, into lower, may be null) and its dual upper bound
  * taken with n_inner inner paths per outer path and date (amc_dual_upper,
- * into upper).                                                             */
+ * into upper).  The dual formulation of §IV (ref. [11]), against the
+ * paper's own upper-bound rule (Eqs. 10-11, §V).                           */
 int amc_price_dual(amc_ctx *ctx, const amc_option *opt, uint64_t outer_seed, int64_t n_outer, int64_t n_inner,
                    uint64_t inner_seed, int prec, amc_result *fit, amc_result *lower, amc_result *upper);
-/* Price, delta and vega of n options (frozen-boundary pathwise adjoint).   */
+/* Price, delta and vega of n options (frozen-boundary pathwise adjoint:
+ * the stopping dates of each path held fixed and e^{-r t} h(S_t)
+ * differentiated along the path, dS/dS0 = S/S0, dS/dsigma = S (W - sigma t)
+ * for the exact GBM step of Eq. 9).  The paper computes no Greeks.
+ * AMC_RULE_LSM or AMC_RULE_EUROPEAN; blocking; host arrays of n.          */
 int amc_greeks(amc_ctx *ctx, const amc_option *opts, int n, int prec,
                double *price, double *delta, double *vega);
+/* amc_greeks on a caller's stream with device inputs and outputs, so that
+ * a framework's autograd can keep spot, volatility and results on the GPU.
+ * S0_dev and sigma_dev (device, n doubles each, either may be null) replace
+ * opts[i].S0 and opts[i].sigma (which are then not read); their values are
+ * checked on the device: an option whose replaced spot or volatility is
+ * not finite and positive gets NaN price, delta and vega and status
+ * AMC_EINVAL, the others are unaffected.  price_dev, delta_dev, vega_dev
+ * (device, n doubles each) receive the results in input order; res_dev
+ * (device, n * AMC_RES_DOUBLES doubles, may be null) also the full result
+ * blocks with each option's status.  All pointers 8-byte aligned.
+ * Ordering, return codes and results as amc_price_batch_device; the
+ * results equal amc_greeks's bit for bit.                                  */
+int amc_greeks_device(amc_ctx *ctx, const amc_option *opts, int n, int prec,
+                      const double *S0_dev, const double *sigma_dev,
+                      double *price_dev, double *delta_dev, double *vega_dev,
+                      double *res_dev, void *stream);
 
 /* ------------------------------------------------------------ serving */
 /* Continuous batching of pricing requests (the paper's many-options
@@ -333,19 +383,31 @@ int amc_serve_stop(amc_ctx *ctx);
  * cudaMalloc/cudaFree, or a plugin hook that holds no amc_ctx (creating one
  * allocates).  The caller passes the paths S_dev (as written by
  * amc_generate_paths) and the result block res_dev[AMC_RES_DOUBLES].
+ *   Sizes: only options that the register-resident sweeps hold are
+ * accepted (amc_plan_sweep succeeds: a mixed LSM option up to
+ * min(SMs, 160) * 7680 paths, 1.17 M on 152 SMs; an FP64 LSM or pathwise
+ * option up to SMs * 8192 paths).  amc_sweep falls back to the streaming
+ * sweep or an uncapped grid beyond those sizes; this call has no fallback
+ * and returns AMC_EINVAL before any device work.
  *   Scratch: a file-scope device array of amc_sweep_noalloc_capacity()
- * bytes (16 MiB) that every GPU loading the library holds until exit.  An
- * option needs 66,304 bytes plus its exchange data: 88*(n_steps+2)*C bytes
- * for the mixed LSM sweep, 96*n_steps*C bytes otherwise, C = the CTA count
- * of amc_plan_sweep (all mixed LSM options fit; an FP64 LSM option with 512
- * dates and 2^20 paths does not); larger options return AMC_EINVAL before
- * any device work.
+ * bytes (16 MiB) that every GPU that runs this call holds until the process
+ * exits.  An option needs 67,840 bytes plus its exchange data:
+ * 88*(n_steps+2)*C bytes for the mixed LSM sweep, 96*n_steps*C bytes
+ * otherwise, C = the CTA count of amc_plan_sweep (all accepted mixed LSM
+ * options fit; an FP64 LSM option with 512 dates and 2^20 paths does not);
+ * an option that needs more returns AMC_EINVAL before any device work.
  *   The first call on a device looks up the array's device address and the
- * SM count (no allocation) and should come before any stream capture.
- * Every call on a device shares the array and clears its counters itself;
- * calls whose work overlaps on the GPU (other streams, or other host
- * threads) race on it and must be serialised by the caller.  Uses the
- * current device; same results as amc_sweep.                               */
+ * SM count (no allocation).  With CUDA's lazy module loading (the default)
+ * that lookup also loads the array, so the driver reserves its 16 MiB at
+ * that first call: make it before any latency-critical loop and before any
+ * stream capture.
+ *   Every call on a device shares the array.  A call clears what must start
+ * at zero (its counters and, for the mixed LSM sweep, the exchange units it
+ * polls) on `stream` before its kernels run.  Calls whose work overlaps on
+ * the GPU (other streams, or other host threads) race on the array and
+ * must be serialised by the caller.  Every device-side wait gives up after
+ * 2 s (status AMC_ETIMEOUT in res_dev).  Uses the current device; results
+ * are bit-identical to amc_sweep's on the same paths.                      */
 int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_dev, int64_t ld,
                       int with_greeks, double *res_dev, void *stream);
 size_t amc_sweep_noalloc_capacity(void);

@@ -102,6 +102,9 @@ SIGNATURES = {
                                           ctypes.c_int, ctypes.c_int, _resp]),
     "amc_price_batch": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _resp]),
     "amc_greeks": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "amc_price_batch_device": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "amc_greeks_device": (ctypes.c_int, [_vp, _optp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         _vp]),
     "amc_serve_start": (ctypes.c_int, [_vp, ctypes.POINTER(amc_serve_config)]),
     "amc_serve_submit": (ctypes.c_int, [_vp, _optp, ctypes.POINTER(_u64)]),
     "amc_serve_poll": (ctypes.c_int, [_vp, _u64, _resp, _dp]),
@@ -448,3 +451,26 @@ def amc_greeks(ctx, options, prec=AMC_MIXED):
     _check(lib().amc_greeks(ctx.handle, arr, n, prec, p.ctypes.data_as(_dp), d.ctypes.data_as(_dp),
                             v.ctypes.data_as(_dp)), "amc_greeks")
     return p, d, v
+
+
+def amc_price_batch_device(ctx, options, res, prec=AMC_MIXED, stream=None):
+    """Price the options on `stream` (a torch.cuda.Stream, a raw handle, or
+    None for the legacy default stream) into the device tensor res (float64,
+    [n, AMC_RES_DOUBLES] contiguous, input order).  Returns without waiting
+    for the GPU."""
+    n = len(options)
+    arr = (amc_option * n)(*[make_option(o) for o in options])
+    _check(lib().amc_price_batch_device(ctx.handle, arr, n, prec, _ptr(res), _stream(stream)),
+           "amc_price_batch_device")
+
+
+def amc_greeks_device(ctx, options, price, delta, vega, prec=AMC_MIXED, S0=None, sigma=None, res=None, stream=None):
+    """Price, delta and vega of the options on `stream` into the device
+    tensors price, delta, vega (float64 [n]); S0 and sigma (float64 [n]
+    device tensors, optional) replace the options' spot and volatility and
+    are checked on the device; res (float64 [n, AMC_RES_DOUBLES], optional)
+    receives the full result blocks.  Returns without waiting for the GPU."""
+    n = len(options)
+    arr = (amc_option * n)(*[make_option(o) for o in options])
+    _check(lib().amc_greeks_device(ctx.handle, arr, n, prec, _ptr(S0), _ptr(sigma), _ptr(price), _ptr(delta),
+                                   _ptr(vega), _ptr(res), _stream(stream)), "amc_greeks_device")

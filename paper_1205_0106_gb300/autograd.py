@@ -7,8 +7,13 @@ and vega that the library's sweep computes in the same pass as the price
 discounted payoff e^{-r t_tau} h(S_tau) is differentiated along the path,
 dS_tau/dS0 = S_tau / S0 and dS_tau/dsigma = S_tau (W_tau - sigma t_tau).
 The forward pass is one library call; the backward pass multiplies the
-incoming gradient by the saved delta and vega.  Argument marshalling only:
-the prices and their derivatives come from the CUDA kernels.
+incoming gradient by the saved delta and vega.  With S0 and sigma on a CUDA
+device the call is amc_greeks_device on PyTorch's current stream: spot and
+volatility are read from the tensors on the GPU and the results are written
+into GPU tensors, with no host round trip and no synchronisation (an
+invalid spot or volatility gives NaN for that option).  CPU tensors take the
+blocking host call.  Argument marshalling only: the prices and their
+derivatives come from the CUDA kernels.
 """
 import torch
 
@@ -23,6 +28,16 @@ class AmericanPrice(torch.autograd.Function):
     @staticmethod
     def forward(ctx, S0, sigma, fixed, amc_ctx, prec):
         import paper_1205_0106_gb300 as pkg
+        if S0.is_cuda:
+            dev = S0.device
+            s0 = S0.detach().to(torch.float64).contiguous()
+            sg = sigma.detach().to(device=dev, dtype=torch.float64).contiguous()
+            p, d, v = (torch.empty(s0.shape[0], dtype=torch.float64, device=dev) for _ in range(3))
+            opts = [dict(o, S0=1.0, sigma=1.0) for o in fixed]     # not read: spot and volatility come from s0, sg
+            pkg.amc_greeks_device(amc_ctx, opts, p, d, v, prec, S0=s0, sigma=sg,
+                                  stream=torch.cuda.current_stream(dev))
+            ctx.save_for_backward(d.to(S0.dtype), v.to(sigma.dtype))
+            return p.to(S0.dtype)
         s0 = S0.detach().to("cpu", torch.float64).tolist()
         sg = sigma.detach().to("cpu", torch.float64).tolist()
         opts = [dict(o, S0=a, sigma=b) for o, a, b in zip(fixed, s0, sg)]

@@ -72,6 +72,7 @@ struct amc_ctx {
     int gcap = 0;
     double *res_host = nullptr;                      // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};  // ordering of the batch streams with a caller's stream
     double timeout_s = 2.0;
     uint32_t poll_ns = 0;                            // exchange poll back-off, ns (AMC_POLL_NS overrides)
     int inject_kind = 0;
@@ -95,11 +96,20 @@ GroupKey group_key(const amc_option &o, const SweepPlan &pl);
 int group_cta_cap(amc_ctx *c, const SweepPlan &pl);
 // Device bytes one option of a group needs (paths and sweep scratch).
 size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec);
+// Device-side inputs and outputs of a batch (the _device calls): spot and
+// volatility overrides and result arrays indexed by input position, any of
+// them null.  `idx` gives the input position of each option of the wave.
+struct DeviceIO {
+    const double *S0 = nullptr, *sigma = nullptr;
+    double *res = nullptr, *price = nullptr, *delta = nullptr, *vega = nullptr;
+    const int32_t *idx = nullptr;      // host, one per option of the wave
+};
 // Launch path generation, sweep and finalize for n options of one group on
-// stream st, memory from ar; results (AMC_RES_DOUBLES per option, input
-// order) in *res_dev.  Asynchronous.  Caller holds c->mu.
+// stream st, memory from ar; results (AMC_RES_DOUBLES per option, wave
+// order) in *res_dev, and scattered to io's arrays when io is given.
+// Asynchronous.  Caller holds c->mu.
 int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int n, int prec, bool greeks,
-                 SubArena &ar, cudaStream_t st, double **res_dev);
+                 SubArena &ar, cudaStream_t st, double **res_dev, const DeviceIO *io = nullptr);
 int result_from(const double *r, amc_result *out);
 
 }  // namespace amc

@@ -79,6 +79,7 @@ struct Job {
     int32_t cta_begin, n_cta;       // sweep CTA group
     int32_t chunks;                 // 4-path chunks per thread
     int32_t inject_date;            // test fault injection (0 = off)
+    int32_t bad;                    // nonzero: a device-side input of this job failed validation
     void *part;                     // cross-CTA partial sums [m][n_cta][kNV] (double-float or double)
     uint32_t *arrive;               // [m] arrival counters (zeroed before launch)
     void *fin;                      // [n_cta][4] final per-CTA sums
@@ -141,6 +142,16 @@ cudaError_t launch_sweep_lsm(const KArgs &a, int total_ctas, int chunks, bool fp
 cudaError_t launch_sweep_pathwise(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
                                   cudaStream_t st);
 cudaError_t launch_finalize(const KArgs &a, cudaStream_t st);
+// Device-side inputs and outputs of a batch wave (sweep.cu): the spot and
+// volatility of job k replaced by S0[idx[k]] and sigma[idx[k]] (either may
+// be null) before path generation, a job whose value is not finite and
+// positive marked bad; after finalize the wave's result blocks res_wave
+// [n][AMC_RES_DOUBLES] scattered to res[idx[k]] (full blocks) and to
+// price/delta/vega[idx[k]] (any of the four may be null).
+cudaError_t launch_patch_inputs(Job *jobs, int n, const int32_t *idx, const double *S0, const double *sigma,
+                                cudaStream_t st);
+cudaError_t launch_scatter_results(const double *res_wave, int n, const int32_t *idx, double *res, double *price,
+                                   double *delta, double *vega, cudaStream_t st);
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
 cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStream_t st);
 

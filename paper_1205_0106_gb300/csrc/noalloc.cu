@@ -17,13 +17,16 @@ namespace {
 
 // Scratch of every amc_sweep_noalloc call on a device: status word, arrival
 // counters, per-CTA final sums and per-date cross-CTA partials.  Each GPU
-// that loads the library holds these bytes until the process exits.
+// that loads the library holds these bytes until the process exits (with
+// lazy module loading, from the first call on that device on).
 constexpr size_t kNoallocBytes = size_t(16) << 20;
 constexpr size_t kOffStatus = 0;
 constexpr size_t kOffArrive = 256;                                  // AMC_MAX_STEPS u32
 constexpr size_t kOffFin = kOffArrive + 4 * AMC_MAX_STEPS;          // [G][4] double
 constexpr size_t kMaxFinCtas = 2048;
 constexpr size_t kOffData = kOffFin + 32 * kMaxFinCtas;             // partials [m][G][kNV] or exchange units
+static_assert(kOffData == 67840, "fixed overhead stated in amc.h");
+constexpr uint64_t kWaitNs = 2000000000ull;                         // device-wait limit, stated in amc.h
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -100,18 +103,19 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
     a.jobs = nullptr;
     a.n_jobs = 1;
     a.max_m = opt->n_steps;
-    a.timeout_ns = 2000000000ull;
-    // the array keeps the previous call's contents: clear what must start at
-    // zero (status, arrival counters); exchange units carry a launch tag that
-    // differs from every earlier call's, and are cleared when the tag wraps
+    a.timeout_ns = kWaitNs;
+    // The array keeps the previous call's contents: clear what must start at
+    // zero (status, arrival counters).  The data region holds the FP64 and
+    // pathwise sweeps' double partials as well as the mixed sweep's tagged
+    // exchange units, and a stale double whose high word happened to equal
+    // this call's tag would pass for a posted unit: a mixed call clears the
+    // units it will poll first.
     if (cudaMemsetAsync(base, 0, kOffFin, st) != cudaSuccess) return AMC_ECUDA;
     if (pl.kind == 2) {
+        if (cudaMemsetAsync(base + kOffData, 0, data_bytes, st) != cudaSuccess) return AMC_ECUDA;
         std::lock_guard<std::mutex> lk(g_mu);
         g_epoch[dev] = (g_epoch[dev] + 1) & ((1u << kEpochBits) - 1u);
-        if (g_epoch[dev] == 0) {
-            if (cudaMemsetAsync(base + kOffData, 0, kNoallocBytes - kOffData, st) != cudaSuccess) return AMC_ECUDA;
-            g_epoch[dev] = 1;
-        }
+        if (g_epoch[dev] == 0) g_epoch[dev] = 1;
         a.epoch = g_epoch[dev];
         a.poll_ns = 0;
     }

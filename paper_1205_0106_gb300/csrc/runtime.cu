@@ -83,15 +83,24 @@ void fill_job_common(const amc_option *o, Job *J) {
 
 uint64_t timeout_ns(const amc_ctx *c) { return (uint64_t)(c->timeout_s * 1e9); }
 
-// Next launch tag of the mixed LSM sweep's exchange units.  Tags never
-// repeat within 2^22 launches; when the counter wraps, every buffer that
-// can hold units (the context scratch and the arena) is cleared first.
-uint32_t next_epoch(amc_ctx *c) {
+// Next launch tag of the mixed LSM sweep's exchange units.  The
+// single-option buffer xch1 only ever holds units, and tags never repeat
+// within 2^22 launches; when the counter wraps it is cleared first.  The
+// batch and serving launches take their units from the arena, whose bytes
+// held other data before, so launch_group clears them on the launch stream
+// before every launch instead.  A test can make the next launch reuse an
+// earlier launch's tag (amc_ctx_inject kind 4; batch and serving launches
+// only, whose units are cleared per launch: xch1 relies on unique tags).
+uint32_t next_epoch(amc_ctx *c, bool from_arena) {
+    if (from_arena && c->inject_kind == 4) {
+        c->inject_kind = 0;
+        c->epoch = (uint32_t)c->inject_arg;
+        return c->epoch;
+    }
     c->epoch = (c->epoch + 1) & ((1u << kEpochBits) - 1u);
     if (c->epoch == 0) {
         cudaDeviceSynchronize();
         cudaMemset(c->xch1, 0, sizeof(uint64_t) * v2_xch_units(AMC_MAX_STEPS, kV2MaxCtas));
-        cudaMemset(c->arena, 0, c->arena_bytes);
         c->epoch = 1;
     }
     return c->epoch;
@@ -100,11 +109,11 @@ uint32_t next_epoch(amc_ctx *c) {
 // Launch the sweep of the packed jobs in `a` (same precision, same plan
 // kind and chunk count, same rule class) and their finalize.
 int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, bool lsm, bool fp64, bool greeks,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool from_arena = false) {
     a.timeout_ns = timeout_ns(c);
     cudaError_t e;
     if (pl.kind == 2) {
-        a.epoch = next_epoch(c);
+        a.epoch = next_epoch(c, from_arena);
         a.poll_ns = c->poll_ns;
         e = launch_sweep_lsm_v2(a, total_ctas, greeks, st);
     } else if (lsm) {
@@ -409,10 +418,20 @@ amc_option make_option(double S0, double K, double r, double sigma, double T, in
 // the arena: the next wave is prepared and launched while the previous one
 // is still on the GPU.  Every option keeps its own CTA group and reduction
 // order, so its result does not depend on the wave it lands in.
-int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, amc_result *out) {
+// Host form (out != nullptr): per wave, results copied to pinned memory and
+// handed out in input order; blocking.  Device form (dev != nullptr):
+// results scattered on the device into the caller's arrays, spot and
+// volatility optionally taken from device memory, the waves ordered after
+// the work already queued on user_st and user_st after them; no host
+// synchronisation.
+int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, amc_result *out,
+              const DeviceIO *dev = nullptr, cudaStream_t user_st = nullptr) {
     AMC_TRY(check_prec(prec));
     for (int i = 0; i < n; ++i) {
-        AMC_TRY(host_validate(&opts[i]));
+        amc_option o = opts[i];
+        if (dev && dev->S0) o.S0 = 1.0;             // checked on the device
+        if (dev && dev->sigma) o.sigma = 0.2;
+        AMC_TRY(host_validate(&o));
         if (greeks && opts[i].rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
     }
     struct Item {
@@ -435,15 +454,20 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         if (a.key.lsm != b.key.lsm) return a.key.lsm && !b.key.lsm;
         return opts[a.idx].n_steps > opts[b.idx].n_steps;
     });
-    for (int i = 0; i < n; ++i) memset(&out[i], 0, sizeof(amc_result));
+    if (out)
+        for (int i = 0; i < n; ++i) memset(&out[i], 0, sizeof(amc_result));
     if (c->inject_kind == 2) {
         c->inject_kind = 0;
         return AMC_ENOMEM;
     }
+    if (dev) {                                                // after the caller's queued work
+        AMC_TRY_CUDA(cudaEventRecord(c->bev[0], user_st));
+        for (int h = 0; h < 2; ++h) AMC_TRY_CUDA(cudaStreamWaitEvent(c->bstream[h], c->bev[0], 0));
+    }
     struct Half {
         cudaStream_t st;
         SubArena ar;
-        std::vector<int> widx;
+        std::vector<int32_t> widx;
         double *res_host = nullptr;
         bool busy = false;
     };
@@ -458,6 +482,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     auto finish = [&](Half &H) -> int {
         if (!H.busy) return AMC_OK;
         H.busy = false;
+        if (dev) return AMC_OK;                               // stream-ordered: nothing to collect
         if (cudaStreamSynchronize(H.st) != cudaSuccess) return AMC_ECUDA;
         int ws = AMC_OK;
         for (size_t k = 0; k < H.widx.size(); ++k) {
@@ -477,7 +502,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         std::vector<const amc_option *> wopts;
         std::vector<SweepPlan> wplans;
         H.widx.clear();
-        size_t bytes = 4096;
+        size_t bytes = 4096 + (dev ? 256 + sizeof(int32_t) * c->batch_cap : 0);   // + input positions (device form)
         int ctas = 0;
         while (pos < items.size() && items[pos].key == key && (int)wopts.size() < c->batch_cap) {
             const amc_option &o = opts[items[pos].idx];
@@ -494,13 +519,21 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         if (status != AMC_OK) break;
         H.ar.top = 0;
         double *res_dev = nullptr;
-        rc = launch_group(c, wopts.data(), wplans.data(), (int)wopts.size(), prec, greeks, H.ar, H.st, &res_dev);
+        DeviceIO wio;
+        if (dev) {
+            wio = *dev;
+            wio.idx = H.widx.data();
+        }
+        rc = launch_group(c, wopts.data(), wplans.data(), (int)wopts.size(), prec, greeks, H.ar, H.st, &res_dev,
+                          dev ? &wio : nullptr);
         if (rc != AMC_OK) { status = rc; break; }
-        H.res_host = c->bres_host[cur];
-        if (cudaMemcpyAsync(H.res_host, res_dev, sizeof(double) * AMC_RES_DOUBLES * wopts.size(),
-                            cudaMemcpyDeviceToHost, H.st) != cudaSuccess) {
-            status = AMC_ECUDA;
-            break;
+        if (!dev) {
+            H.res_host = c->bres_host[cur];
+            if (cudaMemcpyAsync(H.res_host, res_dev, sizeof(double) * AMC_RES_DOUBLES * wopts.size(),
+                                cudaMemcpyDeviceToHost, H.st) != cudaSuccess) {
+                status = AMC_ECUDA;
+                break;
+            }
         }
         H.busy = true;
         cur ^= 1;
@@ -508,6 +541,17 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     for (int h = 0; h < 2; ++h) {
         int rc = finish(half[h]);
         if (status == AMC_OK) status = rc;
+    }
+    if (dev) {
+        // the caller's stream after every wave; so is the context's own
+        // stream, whose calls reuse the arena (the serving slots wait on
+        // the same events when serving starts)
+        for (int h = 0; h < 2; ++h) {
+            if (cudaEventRecord(c->bev[1 + h], c->bstream[h]) != cudaSuccess ||
+                cudaStreamWaitEvent(user_st, c->bev[1 + h], 0) != cudaSuccess ||
+                cudaStreamWaitEvent(c->stream, c->bev[1 + h], 0) != cudaSuccess)
+                return AMC_ECUDA;
+        }
     }
     return status;
 }
@@ -551,7 +595,7 @@ size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec) {
 }
 
 int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int nw, int prec, bool greeks,
-                 SubArena &ar, cudaStream_t st, double **res_out) {
+                 SubArena &ar, cudaStream_t st, double **res_out, const DeviceIO *io) {
     const bool fp64 = prec == AMC_FP64;
     const size_t esz = fp64 ? 8 : 4;
     const SweepPlan plan0 = plans[0];
@@ -576,9 +620,19 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     }
     uint32_t *shift_dev;
     AMC_TRY(ar.alloc(sizeof(uint32_t) * shifts.size(), (void **)&shift_dev));
+    // Exchange units of the mixed LSM sweep: one block for the wave, cleared
+    // below on the launch stream.  The arena bytes held earlier requests'
+    // paths and partial sums, and a stale word whose high half happened to
+    // equal this launch's tag would pass for a posted unit.
+    uint64_t *xch_all = nullptr;
+    size_t xch_words = 0;
+    if (plan0.kind == 2) {
+        for (int k = 0; k < nw; ++k) xch_words += v2_xch_units(opts[k]->n_steps, plans[k].ctas);
+        AMC_TRY(ar.alloc(sizeof(uint64_t) * xch_words, (void **)&xch_all));
+    }
     int64_t tiles = 0;
     int cta = 0, max_slots = 1, max_m = 1;
-    size_t arr_off = 0;
+    size_t arr_off = 0, xch_off = 0;
     for (int k = 0; k < nw; ++k) {
         const amc_option &o = *opts[k];
         Job &J = jobs[k];
@@ -601,7 +655,8 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
         cta += J.n_cta;
         J.greeks = greeks ? 1 : 0;
         if (plan0.kind == 2) {
-            AMC_TRY(ar.alloc(v2_xch_units(o.n_steps, J.n_cta) * 8, (void **)&J.xch));
+            J.xch = xch_all + xch_off;
+            xch_off += v2_xch_units(o.n_steps, J.n_cta);
         } else {
             AMC_TRY(ar.alloc((size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
         }
@@ -614,8 +669,15 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     AMC_TRY_CUDA(cudaMemcpyAsync(shift_dev, shifts.data(), sizeof(uint32_t) * shifts.size(), cudaMemcpyHostToDevice,
                                  st));
     AMC_TRY_CUDA(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(Job) * nw, cudaMemcpyHostToDevice, st));
+    int32_t *idx_dev = nullptr;
+    if (io) {
+        AMC_TRY(ar.alloc(sizeof(int32_t) * nw, (void **)&idx_dev));
+        AMC_TRY_CUDA(cudaMemcpyAsync(idx_dev, io->idx, sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
+        AMC_TRY_CUDA(launch_patch_inputs(jobs_dev, nw, idx_dev, io->S0, io->sigma, st));
+    }
     AMC_TRY_CUDA(cudaMemsetAsync(arrive_all, 0, sizeof(uint32_t) * arrive_words, st));
     AMC_TRY_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t), st));
+    if (xch_words) AMC_TRY_CUDA(cudaMemsetAsync(xch_all, 0, sizeof(uint64_t) * xch_words, st));
     KArgs a;
     memset(&a, 0, sizeof(KArgs));
     a.jobs = jobs_dev;
@@ -626,7 +688,8 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     a.total = tiles;
     a.V = c->V;
     AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));
-    AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st));
+    AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st, true));
+    if (io) AMC_TRY_CUDA(launch_scatter_results(res_dev, nw, idx_dev, io->res, io->price, io->delta, io->vega, st));
     *res_out = res_dev;
     return AMC_OK;
 }
@@ -726,7 +789,9 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
             break;
         }
         for (int k = 0; k < 3; ++k)
-            if (cudaEventCreate(&c->ev[k]) != cudaSuccess) rc = AMC_ECUDA;
+            if (cudaEventCreate(&c->ev[k]) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c->bev[k], cudaEventDisableTiming) != cudaSuccess)
+                rc = AMC_ECUDA;
         if (rc != AMC_OK) break;
         if (arena_bytes == 0) {
             size_t fr = 0, tot = 0;
@@ -767,8 +832,10 @@ int amc_ctx_destroy(amc_ctx *c) {
     cudaFree(c->xch1);
     cudaFree(c->arena);
     if (c->res_host) cudaFreeHost(c->res_host);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        if (c->bev[k]) cudaEventDestroy(c->bev[k]);
+    }
     if (c->stream) cudaStreamDestroy(c->stream);
     for (int h = 0; h < 2; ++h) {
         if (c->bstream[h]) cudaStreamDestroy(c->bstream[h]);
@@ -785,7 +852,8 @@ int amc_ctx_set_timeout(amc_ctx *c, double seconds) {
 }
 
 int amc_ctx_inject(amc_ctx *c, int kind, int64_t arg) {
-    if (!c || kind < 0 || kind > 3) return AMC_EINVAL;
+    if (!c || kind < 0 || kind > 4) return AMC_EINVAL;
+    if (kind == 4 && (arg < 1 || arg >= (int64_t)(1u << kEpochBits))) return AMC_EINVAL;
     c->inject_kind = kind;
     c->inject_arg = arg;
     return AMC_OK;
@@ -990,6 +1058,39 @@ int amc_price_batch(amc_ctx *c, const amc_option *opts, int n, int prec, amc_res
     if (!c || n < 0 || (n > 0 && (!opts || !out))) return AMC_EINVAL;
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     return run_batch(c, opts, n, prec, false, out);
+}
+
+int amc_price_batch_device(amc_ctx *c, const amc_option *opts, int n, int prec, double *res_dev, void *stream) {
+    TraceRange trace_range("amc_price_batch_device");
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || n < 0 || (n > 0 && (!opts || !res_dev)) || ((uintptr_t)res_dev & 7u) != 0) return AMC_EINVAL;
+    if (n == 0) return AMC_OK;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    DeviceIO io;
+    io.res = res_dev;
+    return run_batch(c, opts, n, prec, false, nullptr, &io, (cudaStream_t)stream);
+}
+
+int amc_greeks_device(amc_ctx *c, const amc_option *opts, int n, int prec, const double *S0_dev,
+                      const double *sigma_dev, double *price_dev, double *delta_dev, double *vega_dev, double *res_dev,
+                      void *stream) {
+    TraceRange trace_range("amc_greeks_device");
+    if (c && c->server) return AMC_EBUSY;
+    if (!c || n < 0) return AMC_EINVAL;
+    const void *ptrs[] = {S0_dev, sigma_dev, price_dev, delta_dev, vega_dev, res_dev};
+    for (const void *q : ptrs)
+        if (((uintptr_t)q & 7u) != 0) return AMC_EINVAL;
+    if (n > 0 && (!opts || !price_dev || !delta_dev || !vega_dev)) return AMC_EINVAL;
+    if (n == 0) return AMC_OK;
+    AMC_TRY_CUDA(cudaSetDevice(c->device));
+    DeviceIO io;
+    io.S0 = S0_dev;
+    io.sigma = sigma_dev;
+    io.res = res_dev;
+    io.price = price_dev;
+    io.delta = delta_dev;
+    io.vega = vega_dev;
+    return run_batch(c, opts, n, prec, true, nullptr, &io, (cudaStream_t)stream);
 }
 
 int amc_greeks(amc_ctx *c, const amc_option *opts, int n, int prec, double *price, double *delta, double *vega) {

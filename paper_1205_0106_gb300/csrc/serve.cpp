@@ -214,6 +214,9 @@ int amc_serve_start(amc_ctx *c, const amc_serve_config *cfg) {
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(&sl.res_host, sizeof(double) * AMC_RES_DOUBLES * cfg->max_batch) != cudaSuccess)
             rc = AMC_ECUDA;
+        // the slots reuse the arena: after any device-form batch still in flight
+        for (int h = 1; h < 3 && rc == AMC_OK; ++h)
+            if (cudaStreamWaitEvent(sl.st, c->bev[h], 0) != cudaSuccess) rc = AMC_ECUDA;
     }
     if (rc != AMC_OK) {
         for (Slot &sl : s->slots) {

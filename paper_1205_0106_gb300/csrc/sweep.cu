@@ -26,6 +26,7 @@
 // finalize CTA per option adds them in a fixed order in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <math_constants.h>
 
 #include "devutil.cuh"
 #include "internal.h"
@@ -498,7 +499,50 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ K
         res[2] = s[0][2] / N;
         res[3] = s[0][3] / N;
         res[5] = (double)ld_volatile_int(J.status);
+        if (J.bad) {                    // a device-side input failed validation: no price
+            res[0] = res[1] = res[2] = res[3] = CUDART_NAN;
+            res[5] = (double)AMC_EINVAL;
+        }
     }
+}
+
+// Spot and volatility of each job of a wave from device memory (a caller's
+// tensors), checked here since the host never sees them; a rejected value
+// is replaced by a harmless one so that the wave runs as planned, and the
+// job is marked bad (finalize then writes NaN and AMC_EINVAL).
+__global__ void patch_inputs_kernel(Job *jobs, int n, const int32_t *idx, const double *S0, const double *sigma) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    Job &J = jobs[k];
+    const int i = idx[k];
+    int bad = 0;
+    if (S0) {
+        const double v = S0[i];
+        const bool ok = isfinite(v) && v > 0.0;
+        J.S0 = ok ? v : J.K;
+        bad |= !ok;
+    }
+    if (sigma) {
+        const double v = sigma[i];
+        const bool ok = isfinite(v) && v > 0.0;
+        J.sigma = ok ? v : 0.2;
+        bad |= !ok;
+    }
+    J.bad = bad;
+}
+
+// A wave's result blocks (wave order) to the caller's arrays (input order).
+__global__ void scatter_results_kernel(const double *res_wave, int n, const int32_t *idx, double *res, double *price,
+                                       double *delta, double *vega) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double *r = res_wave + (size_t)k * AMC_RES_DOUBLES;
+    const int i = idx[k];
+    if (res)
+        for (int q = 0; q < AMC_RES_DOUBLES; ++q) res[(size_t)i * AMC_RES_DOUBLES + q] = r[q];
+    if (price) price[i] = r[0];
+    if (delta) delta[i] = r[2];
+    if (vega) vega[i] = r[3];
 }
 
 template <bool FP64, bool GREEKS>
@@ -548,6 +592,20 @@ cudaError_t launch_finalize(const KArgs &a, cudaStream_t st) {
     const int n = a.jobs ? a.n_jobs : 1;
     if (n <= 0) return cudaSuccess;
     finalize_kernel<<<n, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_inputs(Job *jobs, int n, const int32_t *idx, const double *S0, const double *sigma,
+                                cudaStream_t st) {
+    if (n <= 0 || (!S0 && !sigma)) return cudaSuccess;
+    patch_inputs_kernel<<<(n + 127) / 128, 128, 0, st>>>(jobs, n, idx, S0, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_results(const double *res_wave, int n, const int32_t *idx, double *res, double *price,
+                                   double *delta, double *vega, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    scatter_results_kernel<<<(n + 127) / 128, 128, 0, st>>>(res_wave, n, idx, res, price, delta, vega);
     return cudaGetLastError();
 }
 
