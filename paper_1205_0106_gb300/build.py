@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamc.so")
-SOURCES = ["tables.cpp", "pathgen.cu", "sweep.cu", "sweep_v2.cu", "sweep_stream.cu", "value.cu", "dual.cu", "runtime.cu", "launch.cpp", "serve.cpp", "noalloc.cu"]
+SOURCES = ["tables.cpp", "pathgen.cu", "sweep.cu", "sweep_v2.cu", "sweep_cl.cu", "sweep_stream.cu", "value.cu", "dual.cu", "runtime.cu", "launch.cpp", "serve.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 

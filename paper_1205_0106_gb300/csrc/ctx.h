@@ -42,6 +42,7 @@ struct Server;   // serve.cpp
 struct amc_ctx {
     int device = 0;
     int sm_count = 0;
+    int max_cluster = 0;                             // largest cluster sweep the device holds (0: none)
     cudaStream_t stream = nullptr;
     cudaStream_t bstream[2] = {nullptr, nullptr};   // batch waves, double-buffered
     double *bres_host[2] = {nullptr, nullptr};       // pinned wave results

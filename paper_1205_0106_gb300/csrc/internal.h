@@ -53,13 +53,26 @@ constexpr int kSweepThreads = 256;
 constexpr int sweep_ctas_per_sm(int chunks) { return chunks <= 2 ? 4 : (chunks == 4 ? 2 : 1); }
 // kind 1: generic sweep kernels (sweep.cu: FP64 LSM and the pathwise
 // rules), `chunks` 4-path chunks per thread, 256 threads per CTA;
-// kind 2: mixed-precision LSM kernel (sweep_v2.cu), 7680 paths per CTA.
+// kind 2: mixed-precision LSM kernel (sweep_v2.cu), 7680 paths per CTA,
+// exchange through L2, all CTAs co-resident;
+// kind 3: mixed-precision LSM kernel of one cluster per option
+// (sweep_cl.cu), 16384 paths per CTA, `ctas` = the cluster size (up to
+// max_cluster), exchange through distributed shared memory.  Frozen-
+// boundary Greeks use kind 2 (plan_for_greeks).
 struct SweepPlan {
     int kind;
     int chunks;
     int ctas;                       // CTAs for this option
 };
-int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p);
+constexpr int kClThreads = 1024;
+constexpr int kClPPT = 16;
+constexpr int kClPathsPerCta = kClThreads * kClPPT;   // 16384
+constexpr int kClMaxCluster = 16;
+int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p,
+                    int max_cluster = kClMaxCluster);
+// The plan of the Greeks variant: kind 3 has none, so such options take the
+// kind-2 plan (AMC_EINVAL where that does not fit).
+int plan_for_greeks(int64_t n_paths, int sm_count, SweepPlan *p);
 constexpr int kV2MaxCtas = 160;
 
 // ----------------------------------------------------------- device jobs
@@ -153,6 +166,12 @@ cudaError_t launch_patch_inputs(Job *jobs, int n, const int32_t *idx, const doub
 cudaError_t launch_scatter_results(const double *res_wave, int n, const int32_t *idx, double *res, double *price,
                                    double *delta, double *vega, cudaStream_t st);
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st);
+// Cluster sweep (sweep_cl.cu): n_clusters options of `cluster` CTAs each
+// (a.jobs[k] on CTAs k*cluster ..), or a.one on one cluster.
+cudaError_t launch_sweep_cl(const KArgs &a, int cluster, int n_clusters, cudaStream_t st);
+// Largest cluster the current device can hold at once (0: none).
+cudaError_t sweep_cl_max_cluster(int *out);
+size_t sweep_cl_smem();
 cudaError_t launch_value_boundary(const KArgs &a, int ctas, bool fp64, cudaStream_t st);
 
 // Path generation from the LCG-permuted unshifted points (one option).

@@ -34,6 +34,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_scratch_dev[kMaxDevices];   // device address of g_noalloc_scratch, per device
 int g_sm_count[kMaxDevices];
+int g_max_cluster[kMaxDevices];              // largest cluster sweep the device holds, per device
 uint32_t g_epoch[kMaxDevices];               // launch tags of the exchange units, per device
 
 // Once per device, with that device current: look up the array's device
@@ -47,6 +48,8 @@ int setup_device(int dev) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return AMC_ECUDA;
     g_sm_count[dev] = sms;
+    if (sweep_cl_max_cluster(&g_max_cluster[dev]) != cudaSuccess) g_max_cluster[dev] = 0;
+    cudaGetLastError();
     g_scratch_dev[dev] = static_cast<unsigned char *>(p);
     return AMC_OK;
 }
@@ -68,10 +71,11 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
     rc = setup_device(dev);
     if (rc != AMC_OK) return rc;
     SweepPlan pl;
-    rc = host_plan_sweep(opt->n_paths, g_sm_count[dev], prec, opt->rule, &pl);
+    rc = host_plan_sweep(opt->n_paths, g_sm_count[dev], prec, opt->rule, &pl, with_greeks ? 0 : g_max_cluster[dev]);
     if (rc != AMC_OK) return rc;
-    const size_t data_bytes = pl.kind == 2 ? v2_xch_units(opt->n_steps, pl.ctas) * 8
-                                           : (size_t)opt->n_steps * pl.ctas * kNV * 8;
+    const size_t data_bytes = pl.kind == 3 ? 0
+                              : pl.kind == 2 ? v2_xch_units(opt->n_steps, pl.ctas) * 8
+                                             : (size_t)opt->n_steps * pl.ctas * kNV * 8;
     if ((size_t)pl.ctas > kMaxFinCtas || kOffData + data_bytes > kNoallocBytes) return AMC_EINVAL;
 
     unsigned char *base = g_scratch_dev[dev];
@@ -120,7 +124,9 @@ extern "C" int amc_sweep_noalloc(const amc_option *opt, int prec, const void *S_
         a.poll_ns = 0;
     }
     const bool fp64 = prec == AMC_FP64;
-    cudaError_t e = pl.kind == 2 ? launch_sweep_lsm_v2(a, pl.ctas, with_greeks != 0, st)
+    a.timeout_ns = kWaitNs;
+    cudaError_t e = pl.kind == 3 ? launch_sweep_cl(a, pl.ctas, 1, st)
+                    : pl.kind == 2 ? launch_sweep_lsm_v2(a, pl.ctas, with_greeks != 0, st)
                     : opt->rule == AMC_RULE_LSM
                         ? launch_sweep_lsm(a, pl.ctas, pl.chunks, fp64, with_greeks != 0, st)
                         : launch_sweep_pathwise(a, pl.ctas, pl.chunks, fp64, with_greeks != 0, st);

@@ -112,7 +112,9 @@ int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, boo
                   cudaStream_t st, bool from_arena = false) {
     a.timeout_ns = timeout_ns(c);
     cudaError_t e;
-    if (pl.kind == 2) {
+    if (pl.kind == 3) {
+        e = launch_sweep_cl(a, pl.ctas, total_ctas / pl.ctas, st);
+    } else if (pl.kind == 2) {
         a.epoch = next_epoch(c, from_arena);
         a.poll_ns = c->poll_ns;
         e = launch_sweep_lsm_v2(a, total_ctas, greeks, st);
@@ -253,7 +255,8 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     }
     SweepPlan pl;
     bool big = false;                                 // too many paths for the co-resident plans
-    if (host_plan_sweep(o->n_paths, c->sm_count, prec, o->rule, &pl) != AMC_OK || pl.ctas > c->gcap) {
+    if (host_plan_sweep(o->n_paths, c->sm_count, prec, o->rule, &pl, greeks ? 0 : c->max_cluster) != AMC_OK ||
+        pl.ctas > c->gcap) {
         if (greeks) return AMC_EINVAL;                // frozen-boundary Greeks: register-resident sizes only
         if (o->rule == AMC_RULE_LSM) return do_sweep_stream(c, o, prec, S, ld, res, st, coef);
         // the pathwise rules need no co-resident CTAs: any grid, 8 paths per thread
@@ -443,7 +446,8 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     for (int i = 0; i < n; ++i) {
         Item it;
         it.idx = i;
-        AMC_TRY(host_plan_sweep(opts[i].n_paths, c->sm_count, prec, opts[i].rule, &it.pl));
+        AMC_TRY(host_plan_sweep(opts[i].n_paths, c->sm_count, prec, opts[i].rule, &it.pl,
+                                greeks ? 0 : c->max_cluster));
         it.key = group_key(opts[i], it.pl);
         items.push_back(it);
     }
@@ -574,21 +578,23 @@ int result_from(const double *r, amc_result *out) {
 GroupKey group_key(const amc_option &o, const SweepPlan &pl) {
     GroupKey k;
     k.kind = pl.kind;
-    k.type = pl.kind == 2 ? o.type : 0;
-    k.chunks = pl.chunks;
+    k.type = pl.kind >= 2 ? o.type : 0;
+    k.chunks = pl.kind == 3 ? pl.ctas : pl.chunks;    // one cluster size per cluster launch
     k.lsm = o.rule == AMC_RULE_LSM;
     return k;
 }
 
 int group_cta_cap(amc_ctx *c, const SweepPlan &pl) {
+    if (pl.kind == 3) return 1 << 30;                 // clusters run independently: no co-residency cap
     return pl.kind == 2 ? std::min(c->sm_count, kV2MaxCtas) : sweep_ctas_per_sm(pl.chunks) * c->sm_count;
 }
 
 size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec) {
     const size_t esz = prec == AMC_FP64 ? 8 : 4;
     size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);            // paths
-    need += pl.kind == 2 ? align_up(v2_xch_units(o.n_steps, pl.ctas) * 8, 256)            // exchange units
-                         : align_up((size_t)o.n_steps * pl.ctas * kNV * 8, 256);          // partials
+    need += pl.kind == 3 ? 0                                                              // on-chip exchange
+            : pl.kind == 2 ? align_up(v2_xch_units(o.n_steps, pl.ctas) * 8, 256)          // exchange units
+                           : align_up((size_t)o.n_steps * pl.ctas * kNV * 8, 256);        // partials
     need += 2 * align_up((size_t)o.n_steps * 4, 256);                                      // arrive + shifts
     need += align_up((size_t)pl.ctas * 32, 256) + align_up(sizeof(Job), 256) + 256;       // fin, job, result
     return need;
@@ -657,7 +663,7 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
         if (plan0.kind == 2) {
             J.xch = xch_all + xch_off;
             xch_off += v2_xch_units(o.n_steps, J.n_cta);
-        } else {
+        } else if (plan0.kind == 1) {
             AMC_TRY(ar.alloc((size_t)o.n_steps * J.n_cta * kNV * 8, &J.part));
         }
         J.arrive = arrive_all + arr_off;
@@ -740,7 +746,7 @@ int amc_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, int32_t *c
     int rc = host_plan_sweep(n_paths, sm_count, prec, rule, &p);
     if (rc != AMC_OK) return rc;
     if (ctas) *ctas = p.ctas;
-    if (paths_per_thread) *paths_per_thread = p.kind == 2 ? kV2PPT : 4 * p.chunks;
+    if (paths_per_thread) *paths_per_thread = p.kind == 3 ? kClPPT : (p.kind == 2 ? kV2PPT : 4 * p.chunks);
     return AMC_OK;
 }
 
@@ -775,6 +781,8 @@ int amc_ctx_create(int device, size_t arena_bytes, amc_ctx **out) {
             break;
         }
         c->gcap = 4 * c->sm_count;
+        if (sweep_cl_max_cluster(&c->max_cluster) != cudaSuccess) c->max_cluster = 0;
+        cudaGetLastError();
         size_t part_bytes = (size_t)AMC_MAX_STEPS * c->gcap * kNV * 8;
         if (cudaMalloc(&c->shift1, 4 * AMC_MAX_STEPS) != cudaSuccess ||
             cudaMalloc(&c->part1, part_bytes) != cudaSuccess ||

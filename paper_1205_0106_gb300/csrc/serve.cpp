@@ -240,7 +240,7 @@ int amc_serve_submit(amc_ctx *c, const amc_option *opt, uint64_t *ticket) {
     if (rc != AMC_OK) return rc;
     Request r;
     r.opt = *opt;
-    rc = host_plan_sweep(opt->n_paths, c->sm_count, s->cfg.prec, opt->rule, &r.plan);
+    rc = host_plan_sweep(opt->n_paths, c->sm_count, s->cfg.prec, opt->rule, &r.plan, c->max_cluster);
     if (rc != AMC_OK) return rc;
     r.key = group_key(*opt, r.plan);
     r.bytes = option_bytes(*opt, r.plan, s->cfg.prec);

@@ -2,6 +2,7 @@
 // Brownian-bridge schedule and its depth-first evaluation plan, option
 // validation and the sweep launch plan.  Pure host code (no CUDA calls), so
 // every function here is testable without a GPU through the C ABI.
+#include <algorithm>
 #include <math.h>
 #include <string.h>
 
@@ -197,8 +198,15 @@ int64_t host_ld(int64_t n_paths) { return (n_paths + 31) / 32 * 32; }
 // count fits the co-resident capacity sweep_ctas_per_sm(chunks) * SMs.
 // Depends on the path count, precision, rule and SM count only, so an
 // option's reduction order is the same alone or batched.
-int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p) {
+int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p, int max_cluster) {
     if (n_paths < 1 || sm_count < 1) return AMC_EINVAL;
+    if (prec == AMC_MIXED && rule == AMC_RULE_LSM && max_cluster >= 1 &&
+        n_paths <= (int64_t)std::min(max_cluster, kClMaxCluster) * kClPathsPerCta) {
+        p->kind = 3;                                  // one cluster per option
+        p->chunks = kClPPT;
+        p->ctas = (int)((n_paths + kClPathsPerCta - 1) / kClPathsPerCta);
+        return AMC_OK;
+    }
     if (prec == AMC_MIXED && rule == AMC_RULE_LSM) {
         const int64_t g = (n_paths + kV2PathsPerCta - 1) / kV2PathsPerCta;
         if (g > sm_count || g > kV2MaxCtas) return AMC_EINVAL;   // per-path state must stay on chip
@@ -219,6 +227,10 @@ int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan
         }
     }
     return AMC_EINVAL;                                // too many paths to keep in registers
+}
+
+int plan_for_greeks(int64_t n_paths, int sm_count, SweepPlan *p) {
+    return host_plan_sweep(n_paths, sm_count, AMC_MIXED, AMC_RULE_LSM, p, 0);
 }
 
 }  // namespace amc

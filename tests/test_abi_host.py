@@ -113,7 +113,12 @@ def test_sweep_plan_is_a_function_of_paths(amc):
         assert ctas * 256 * ppt < n + 256 * ppt + 1
         assert ppt in (4, 8, 16, 32)
         ctas, ppt = amc.amc_plan_sweep(n, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM)
-        assert ppt == 8 and ctas == -(-n // 7680) and ctas <= 152
+        if n <= 2 ** 18:        # one cluster of up to 16 CTAs of 16384 paths
+            assert ppt == 16 and ctas == -(-n // 16384) and ctas <= 16
+        else:                   # CTAs of 7680 paths exchanging through L2
+            assert ppt == 8 and ctas == -(-n // 7680) and ctas <= 152
+    assert amc.amc_plan_sweep(2 ** 18, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM) == (16, 16)
+    assert amc.amc_plan_sweep(2 ** 18 + 1, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM) == (35, 8)
     assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_FP64, amc.AMC_RULE_LSM) == (512, 8)
     assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_MIXED, amc.AMC_RULE_LSM) == (137, 8)
     assert amc.amc_plan_sweep(2 ** 20, 152, amc.AMC_MIXED, amc.AMC_RULE_EUROPEAN) == (512, 8)

@@ -1,8 +1,10 @@
 """Stale cross-CTA exchange data on the batch and serving paths.
 
-The mixed-precision LSM sweep sums each date's per-CTA partials through
-64-bit exchange units: an FP32 payload under a 32-bit tag made of the
-launch's tag and the exchange index, polled until every tag matches.  The
+The mixed-precision LSM sweep of an option above 2^18 paths sums each date's
+per-CTA partials through 64-bit exchange units in global memory: an FP32
+payload under a 32-bit tag made of the launch's tag and the exchange index,
+polled until every tag matches (smaller options exchange on chip, within
+one thread-block cluster, and the Greeks variant always uses the units).  The
 batch and serving launches take their units from the context arena, whose
 bytes held earlier requests' paths, partial sums and units.  The library
 clears a launch's units before the launch; these tests make the worst case
@@ -35,16 +37,18 @@ def amc():
     return amc
 
 
-def _layout(n, seed, n_paths_max):
-    """n mixed-LSM options (dates, paths, type, basis from the batch draw) and
-    a second set with the same layouts but other prices, rates and shifts
-    (moneyness 0.9..1.1, volatility 15..35 %, where the estimator is stable
-    at FP32 precision)."""
+def _layout(n, seed, n_paths, max_steps=60):
+    """n mixed-LSM options (dates up to max_steps, type and basis from the
+    batch draw, n_paths paths each) and a second set with the same layouts
+    but other prices, rates and shifts (moneyness 0.9..1.1, volatility
+    15..35 %, where the estimator is stable at FP32 precision).  Above 2^18
+    paths the mixed sweep exchanges through tagged units in the arena (at
+    most 2^18, one cluster per option exchanges on chip)."""
     base = workloads.batch_options(n=n)
     rng = np.random.default_rng(seed)
     a, b = [], []
     for k, o in enumerate(base):
-        o = workloads.scaled(o, n_paths=min(o.n_paths, n_paths_max))
+        o = workloads.scaled(o, n_paths=n_paths, n_steps=min(o.n_steps, max_steps))
         a.append(o)
         K = float(rng.uniform(80, 120))
         b.append(workloads.Option(K * float(rng.uniform(0.9, 1.1)), K, float(rng.uniform(0, 0.08)),
@@ -59,8 +63,8 @@ def _alone(amc, ctx, o, prec=1):
 
 
 def test_batch_with_replayed_tags_equals_alone_and_oracle(amc):
-    first, second = _layout(24, 101, 2 ** 16)
-    with amc.Context(0, arena_bytes=1 << 30) as ctx:
+    first, second = _layout(24, 101, 300000)
+    with amc.Context(0, arena_bytes=4 << 30) as ctx:
         alone = [_alone(amc, ctx, o) for o in second]
         ctx.inject(4, REPLAYED_TAG)
         res_first = amc.amc_price_batch(ctx, first, amc.AMC_MIXED)
@@ -78,7 +82,7 @@ def test_batch_with_replayed_tags_equals_alone_and_oracle(amc):
 
 
 def test_greeks_with_replayed_tags_equal_alone(amc):
-    first, second = _layout(8, 102, 2 ** 15)
+    first, second = _layout(8, 102, 2 ** 15, max_steps=365)
     first = [workloads.Option(**{**o.as_dict(), "type": workloads.PUT}) for o in first]
     second = [workloads.Option(**{**o.as_dict(), "type": workloads.PUT}) for o in second]
     with amc.Context(0, arena_bytes=1 << 30) as ctx:
@@ -93,13 +97,13 @@ def test_greeks_with_replayed_tags_equal_alone(amc):
 def test_served_mix_with_replayed_tags_equals_alone(amc):
     """A served mix whose first launch reuses the tag of a batch launch that
     ran just before it on the same arena: every result equals alone."""
-    first, second = _layout(32, 103, 2 ** 15)
-    with amc.Context(0, arena_bytes=1 << 30) as ctx:
+    first, second = _layout(16, 103, 300000)
+    with amc.Context(0, arena_bytes=4 << 30) as ctx:
         alone = [_alone(amc, ctx, o) for o in second]
         ctx.inject(4, REPLAYED_TAG)
         amc.amc_price_batch(ctx, first, amc.AMC_MIXED)
         ctx.inject(4, REPLAYED_TAG)
-        amc.amc_serve_start(ctx, slots=2, max_batch=8, prec=amc.AMC_MIXED)
+        amc.amc_serve_start(ctx, slots=2, max_batch=4, prec=amc.AMC_MIXED)
         tickets = {}
         for i, o in enumerate(second):
             tickets[amc.amc_serve_submit(ctx, o)] = i
