@@ -192,9 +192,14 @@ def cpu_baseline(opt, n_sample=None):
     return out, (res["price"] if n_sample == opt.n_paths else None)
 
 
-def batch_and_greeks(amc, device, reps=2):
+def batch_and_greeks(amc, device, hbm, peak_kind, reps=2):
     """The 4096-option batch and the 1024-option Greeks workloads through their host calls
-    (host buffers in and out, so wall time), each after one warm-up call."""
+    (host buffers in and out, so wall time), each after one warm-up call.  The batch's
+    path-generation and sweep launches are also timed on the device (the context's
+    opt-in profiling: CUDA events around every launch on its stream): the sweep's
+    roofline is its algorithmic bytes (4 B per path-step, S read once) over the summed
+    sweep-launch time, path generation's its 4 B per path-step written (with profiling
+    on, the waves run one after another, so the launch times are not shared)."""
     bctx = amc.Context(device, arena_bytes=32 << 30)
     out = {}
     opts = workloads.batch_options()
@@ -205,8 +210,26 @@ def batch_and_greeks(amc, device, reps=2):
         res = amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
     dt = (time.perf_counter() - t) / reps
     failed = sum(r["status"] != 0 for r in res)
+    bctx.profile()
+    bctx.set_profiling(True)
+    t = time.perf_counter()
+    amc.amc_price_batch(bctx, opts, amc.AMC_MIXED)
+    dt_prof = time.perf_counter() - t
+    prof = bctx.profile()
+    bctx.set_profiling(False)
+    sweep_gbs = 4.0 * prof["sweep_path_steps"] / (prof["sweep_ms"] * 1e-3) / 1e9
+    gen_gbs = 4.0 * prof["gen_path_steps"] / (prof["gen_ms"] * 1e-3) / 1e9
     out["batch"] = {"options": len(opts), "path_steps": steps, "s": dt, "value": steps / dt, "unit": METRIC,
-                    "failed": failed, "workload": "4096 options, seed 3, 2^14..2^18 paths, 12..365 dates, p = 3"}
+                    "failed": failed, "workload": "4096 options, seed 3, 2^14..2^18 paths, 12..365 dates, p = 3",
+                    "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": sweep_gbs / hbm, "traffic": None, "peak_kind": peak_kind,
+                                 "kernel": "sweep_cl_kernel (one cluster per option, on-chip exchange)",
+                                 "sweep_launches": prof["sweep_launches"], "sweep_ms": prof["sweep_ms"],
+                                 "algorithmic_bytes": 4.0 * prof["sweep_path_steps"]},
+                    "roofline_pathgen": {"bound": "hbm", "achieved": gen_gbs, "peak": hbm, "unit": "GB/s",
+                                         "frac": gen_gbs / hbm, "peak_kind": peak_kind, "kernel": "pathgen_kernel",
+                                         "launches": prof["gen_launches"], "ms": prof["gen_ms"]},
+                    "s_with_profiling": dt_prof}
     gopts = workloads.greeks_options()
     gsteps = sum(o.path_steps for o in gopts)
     amc.amc_greeks(bctx, gopts, amc.AMC_MIXED)
@@ -657,13 +680,19 @@ def run_amc(args):
     ld = amc.amc_path_ld(opt.n_paths)
     units = opt.n_paths * opt.n_steps
 
-    def time_steps(prec, steps, warmup, split=False):
+    def time_steps(prec, steps, warmup, split=False, streaming=False):
+        # streaming: every sweep through the streaming design (context injection kind 3)
         dt = torch.float64 if prec == amc.AMC_FP64 else torch.float32
         S = torch.empty((opt.n_steps, ld), dtype=dt, device="cuda")
         res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+
+        def price():
+            if streaming:
+                ctx.inject(3)
+            amc.amc_price_device(ctx, opt, prec, S, res, stream=stream)
         with torch.cuda.stream(stream):
             for _ in range(warmup):
-                amc.amc_price_device(ctx, opt, prec, S, res, stream=stream)
+                price()
             stream.synchronize()
             if dist is not None:
                 dist.barrier()
@@ -679,7 +708,7 @@ def run_amc(args):
             else:
                 ev[0].record(stream)
                 for _ in range(steps):
-                    amc.amc_price_device(ctx, opt, prec, S, res, stream=stream)
+                    price()
                 ev[1].record(stream)
             stream.synchronize()
             torch.cuda.synchronize()
@@ -800,10 +829,16 @@ def run_amc(args):
 
     # per-kernel times (same steps, generate and sweep timed apart)
     _, gen_ms, sweep_ms, _ = time_steps(amc.AMC_MIXED, max(3, args.steps // 2), 2, split=True)
-    # FP64 GPU baseline on identical points
+    # FP64 GPU baseline on identical points: the first sweep design (FP64
+    # everywhere, counter-based exchange) and the streaming sweep in FP64
+    # (the fastest FP64 design: one pass and one solve per date, its cash
+    # flows in device memory), each after FP64 path generation
     f_ms, _, _, fres = time_steps(amc.AMC_FP64, max(3, args.steps // 4), 2)
     fp64_ms = f_ms / max(3, args.steps // 4)
     fp64_price = amc.res_to_dict(fres.cpu().numpy())["price"]
+    fs_ms, _, _, fsres = time_steps(amc.AMC_FP64, max(3, args.steps // 4), 2, streaming=True)
+    fp64s_ms = fs_ms / max(3, args.steps // 4)
+    fp64s_price = amc.res_to_dict(fsres.cpu().numpy())["price"]
 
     # end to end through the host API: option in, price out (host buffers)
     for _ in range(2):
@@ -849,7 +884,11 @@ def run_amc(args):
             "price": price["price"], "std_err": price["std_err"],
             "err_vs_oracle_over_K": None,
             "fp64": {"value": units * ws / (fp64_ms * 1e-3), "ms_per_step": fp64_ms, "price": fp64_price,
-                     "mixed_over_fp64": fp64_ms / ms_per_step},
+                     "mixed_over_fp64": fp64_ms / ms_per_step, "design": "first sweep design, FP64 throughout",
+                     "streaming": {"value": units * ws / (fp64s_ms * 1e-3), "ms_per_step": fp64s_ms,
+                                   "price": fp64s_price, "mixed_over_fp64": fp64s_ms / ms_per_step,
+                                   "design": "streaming sweep in FP64 (one pass and one solve per date)"},
+                     "mixed_over_fastest_fp64": min(fp64_ms, fp64s_ms) / ms_per_step},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 64},
             "gpu_launches": 3 * args.steps,
             "roofline": dominant, "roofline_sweep": rl_sweep, "roofline_pathgen": rl_gen,
@@ -867,10 +906,15 @@ def run_amc(args):
         sv = serve_replay(amc, sctx, [0.0] * 8, sopts[:8])
         sv = serve_replay(amc, sctx, list(times), sopts)
         sv["workload"] = "Poisson 2000 req/s, %.0f s of the seed-4 request stream" % args.serve_seconds
+        # saturated: the first 2 s of the stream offered at ten times the rate (capacity, not offered load)
+        n2 = sum(1 for t in times if t < 2.0)
+        sat = serve_replay(amc, sctx, [t / 10.0 for t in times[:n2]], sopts[:n2])
+        sat["workload"] = "the first 2 s of the seed-4 stream offered at 10x the rate (20000 req/s)"
+        sv["saturated"] = sat
         line["serving"] = sv
         sctx.close()
     if not args.no_batch:
-        line.update(batch_and_greeks(amc, local))
+        line.update(batch_and_greeks(amc, local, hbm, peak_kind))
         line["fig1"] = fig1_bench(amc, local)
         line["table2"] = table2_bench(amc, ctx)
     if not args.no_cpu_baseline:

@@ -132,6 +132,19 @@ int amc_ctx_set_timeout(amc_ctx *ctx, double seconds);
  *           fresh (results must not change);
  *   kind 0: clear.                                                          */
 int amc_ctx_inject(amc_ctx *ctx, int kind, int64_t arg);
+/* Opt-in device timing of the hot path's launches (off by default): with
+ * profiling on, every path-generation launch and every sweep launch of
+ * this context (single options, batches, Greeks, serving) is bracketed by
+ * CUDA events on its stream, with its work in path-steps (the sum of
+ * n_paths * n_steps over the options it covers); the waves of a batch then
+ * run one after another on one stream, so that each launch's time is its
+ * own rather than shared with an overlapping launch.  amc_ctx_profile waits for
+ * the recorded launches, returns the summed device times (ms), launch
+ * counts and path-steps of each kind since the previous call, and clears
+ * them; any pointer may be null.                                           */
+int amc_ctx_set_profiling(amc_ctx *ctx, int enable);
+int amc_ctx_profile(amc_ctx *ctx, double *gen_ms, double *sweep_ms, int64_t *gen_launches,
+                    int64_t *sweep_launches, int64_t *gen_path_steps, int64_t *sweep_path_steps);
 /* Bytes of the arena currently free / total.                               */
 int amc_ctx_memory(amc_ctx *ctx, size_t *free_bytes, size_t *total_bytes);
 

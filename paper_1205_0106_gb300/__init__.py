@@ -78,6 +78,9 @@ SIGNATURES = {
     "amc_ctx_set_timeout": (ctypes.c_int, [_vp, ctypes.c_double]),
     "amc_ctx_inject": (ctypes.c_int, [_vp, ctypes.c_int, _i64]),
     "amc_ctx_memory": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "amc_ctx_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "amc_ctx_profile": (ctypes.c_int, [_vp, _dp, _dp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                       ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "amc_validate_option": (ctypes.c_int, [_optp]),
     "amc_path_ld": (_i64, [_i64]),
     "amc_path_bytes": (ctypes.c_size_t, [ctypes.c_int, _i64, ctypes.c_int]),
@@ -249,6 +252,19 @@ class Context:
 
     def inject(self, kind, arg=0):
         _check(lib().amc_ctx_inject(self.handle, kind, arg), "amc_ctx_inject")
+
+    def set_profiling(self, enable=True):
+        _check(lib().amc_ctx_set_profiling(self.handle, 1 if enable else 0), "amc_ctx_set_profiling")
+
+    def profile(self):
+        """Device time (ms), launches and path-steps of the path-generation
+        and sweep launches since the previous call (profiling on)."""
+        g, s = ctypes.c_double(), ctypes.c_double()
+        n = [_i64() for _ in range(4)]
+        _check(lib().amc_ctx_profile(self.handle, ctypes.byref(g), ctypes.byref(s), *[ctypes.byref(x) for x in n]),
+               "amc_ctx_profile")
+        return {"gen_ms": g.value, "sweep_ms": s.value, "gen_launches": n[0].value, "sweep_launches": n[1].value,
+                "gen_path_steps": n[2].value, "sweep_path_steps": n[3].value}
 
     def memory(self):
         f, t = ctypes.c_size_t(), ctypes.c_size_t()

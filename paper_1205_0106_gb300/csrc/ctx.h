@@ -78,6 +78,13 @@ struct amc_ctx {
     uint32_t poll_ns = 0;                            // exchange poll back-off, ns (AMC_POLL_NS overrides)
     int inject_kind = 0;
     int64_t inject_arg = 0;
+    // opt-in profiling of path generation and sweep launches (events)
+    struct Prof {
+        bool on = false;
+        std::vector<cudaEvent_t> pool;                // free events
+        struct Rec { cudaEvent_t a, b; int kind; int64_t units; };
+        std::vector<Rec> recs;                        // kind 0: path generation, 1: sweep
+    } prof;
     std::mutex mu;                                   // launches and tables
     amc::Server *server = nullptr;                   // running serving loop, if any
 };
@@ -112,5 +119,9 @@ struct DeviceIO {
 int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int n, int prec, bool greeks,
                  SubArena &ar, cudaStream_t st, double **res_dev, const DeviceIO *io = nullptr);
 int result_from(const double *r, amc_result *out);
+// Profiling (no-op unless enabled): an event before a launch, and after it
+// the record of its kind and work units (path-steps).  Caller holds c->mu.
+cudaEvent_t prof_begin(amc_ctx *c, cudaStream_t st);
+void prof_end(amc_ctx *c, cudaEvent_t a, int kind, int64_t units, cudaStream_t st);
 
 }  // namespace amc

@@ -109,8 +109,9 @@ uint32_t next_epoch(amc_ctx *c, bool from_arena) {
 // Launch the sweep of the packed jobs in `a` (same precision, same plan
 // kind and chunk count, same rule class) and their finalize.
 int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, bool lsm, bool fp64, bool greeks,
-                  cudaStream_t st, bool from_arena = false) {
+                  cudaStream_t st, bool from_arena = false, int64_t units = 0) {
     a.timeout_ns = timeout_ns(c);
+    cudaEvent_t pe = prof_begin(c, st);
     cudaError_t e;
     if (pl.kind == 3) {
         e = launch_sweep_cl(a, pl.ctas, total_ctas / pl.ctas, st);
@@ -124,6 +125,7 @@ int launch_sweeps(amc_ctx *c, KArgs &a, const SweepPlan &pl, int total_ctas, boo
         e = launch_sweep_pathwise(a, total_ctas, pl.chunks, fp64, greeks, st);
     }
     AMC_TRY_CUDA(e);
+    prof_end(c, pe, 1, units, st);
     AMC_TRY_CUDA(launch_finalize(a, st));
     return AMC_OK;
 }
@@ -174,7 +176,9 @@ int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, 
     a.max_slots = b->nslots;
     a.total = J.n_tiles;
     a.V = c->V;
+    cudaEvent_t pe = prof_begin(c, st);
     AMC_TRY_CUDA(launch_pathgen(a, prec == AMC_FP64, c->sm_count, st));
+    prof_end(c, pe, 0, o->n_paths * (int64_t)o->n_steps, st);
     return AMC_OK;
 }
 
@@ -297,7 +301,8 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     if (pl.kind == 1 && o->rule == AMC_RULE_LSM)
         AMC_TRY_CUDA(cudaMemsetAsync(c->arrive1, 0, sizeof(uint32_t) * o->n_steps, st));
     AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
-    return launch_sweeps(c, a, pl, pl.ctas, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st);
+    return launch_sweeps(c, a, pl, pl.ctas, o->rule == AMC_RULE_LSM, prec == AMC_FP64, greeks, st, false,
+                         o->n_paths * (int64_t)o->n_steps);
 }
 
 
@@ -478,7 +483,9 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
     Half half[2];
     const size_t hb = c->arena_bytes / 2 / 4096 * 4096;
     for (int h = 0; h < 2; ++h) {
-        half[h].st = c->bstream[h];
+        // with profiling on, the waves run one after another on one stream,
+        // so that every launch's measured time is its own
+        half[h].st = c->prof.on ? c->bstream[0] : c->bstream[h];
         half[h].ar.base = c->arena + h * hb;
         half[h].ar.size = hb;
     }
@@ -573,6 +580,32 @@ int result_from(const double *r, amc_result *out) {
     out->degenerate_dates = (int32_t)r[4];
     out->status = (int32_t)r[5];
     return out->status;
+}
+
+cudaEvent_t prof_begin(amc_ctx *c, cudaStream_t st) {
+    if (!c->prof.on) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!c->prof.pool.empty()) {
+        e = c->prof.pool.back();
+        c->prof.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    if (cudaEventRecord(e, st) != cudaSuccess) {
+        c->prof.pool.push_back(e);
+        return nullptr;
+    }
+    return e;
+}
+
+void prof_end(amc_ctx *c, cudaEvent_t a, int kind, int64_t units, cudaStream_t st) {
+    if (!a) return;
+    cudaEvent_t b = prof_begin(c, st);
+    if (!b) {
+        c->prof.pool.push_back(a);
+        return;
+    }
+    c->prof.recs.push_back({a, b, kind, units});
 }
 
 GroupKey group_key(const amc_option &o, const SweepPlan &pl) {
@@ -693,8 +726,12 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     a.jobs_type = opts[0]->type;
     a.total = tiles;
     a.V = c->V;
+    int64_t units = 0;
+    for (int k = 0; k < nw; ++k) units += opts[k]->n_paths * (int64_t)opts[k]->n_steps;
+    cudaEvent_t pe = prof_begin(c, st);
     AMC_TRY_CUDA(launch_pathgen(a, fp64, c->sm_count, st));
-    AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st, true));
+    prof_end(c, pe, 0, units, st);
+    AMC_TRY(launch_sweeps(c, a, plan0, cta, lsm, fp64, greeks, st, true, units));
     if (io) AMC_TRY_CUDA(launch_scatter_results(res_dev, nw, idx_dev, io->res, io->price, io->delta, io->vega, st));
     *res_out = res_dev;
     return AMC_OK;
@@ -844,6 +881,11 @@ int amc_ctx_destroy(amc_ctx *c) {
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         if (c->bev[k]) cudaEventDestroy(c->bev[k]);
     }
+    for (auto &r : c->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
     for (int h = 0; h < 2; ++h) {
         if (c->bstream[h]) cudaStreamDestroy(c->bstream[h]);
@@ -865,6 +907,41 @@ int amc_ctx_inject(amc_ctx *c, int kind, int64_t arg) {
     c->inject_kind = kind;
     c->inject_arg = arg;
     return AMC_OK;
+}
+
+int amc_ctx_set_profiling(amc_ctx *c, int enable) {
+    if (!c) return AMC_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->prof.on = enable != 0;
+    return AMC_OK;
+}
+
+int amc_ctx_profile(amc_ctx *c, double *gen_ms, double *sweep_ms, int64_t *gen_launches, int64_t *sweep_launches,
+                    int64_t *gen_units, int64_t *sweep_units) {
+    if (!c) return AMC_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return AMC_ECUDA;
+    double ms[2] = {0.0, 0.0};
+    int64_t n[2] = {0, 0}, u[2] = {0, 0};
+    int rc = AMC_OK;
+    for (auto &r : c->prof.recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            rc = AMC_ECUDA;
+        ms[r.kind] += t;
+        n[r.kind] += 1;
+        u[r.kind] += r.units;
+        c->prof.pool.push_back(r.a);
+        c->prof.pool.push_back(r.b);
+    }
+    c->prof.recs.clear();
+    if (gen_ms) *gen_ms = ms[0];
+    if (sweep_ms) *sweep_ms = ms[1];
+    if (gen_launches) *gen_launches = n[0];
+    if (sweep_launches) *sweep_launches = n[1];
+    if (gen_units) *gen_units = u[0];
+    if (sweep_units) *sweep_units = u[1];
+    return rc;
 }
 
 int amc_ctx_memory(amc_ctx *c, size_t *free_bytes, size_t *total_bytes) {

@@ -132,3 +132,23 @@ def test_context_calls_after_a_device_batch_are_ordered_after_it(env):
     got = res.cpu().numpy()
     for i, h in enumerate(host):
         assert got[i][0] == h["price"], (i, got[i], h)
+
+
+def test_profiling_counts_every_launch_and_its_path_steps(env):
+    """Opt-in device timing: a batch's path-generation and sweep launches are
+    timed and their path-steps add up to the batch's; off again, nothing is
+    recorded."""
+    amc, ctx, torch = env
+    opts = _opts(20)
+    ctx.profile()                                        # clear
+    ctx.set_profiling(True)
+    res = amc.amc_price_batch(ctx, opts, amc.AMC_MIXED)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    steps = sum(o.n_paths * o.n_steps for o in opts)
+    assert all(r["status"] == 0 for r in res)
+    assert prof["gen_path_steps"] == steps and prof["sweep_path_steps"] == steps
+    assert prof["gen_launches"] >= 1 and prof["sweep_launches"] == prof["gen_launches"]
+    assert prof["gen_ms"] > 0.0 and prof["sweep_ms"] > 0.0
+    amc.amc_price_batch(ctx, opts, amc.AMC_MIXED)
+    assert ctx.profile()["sweep_launches"] == 0

@@ -86,11 +86,14 @@ def test_scaled_keeps_the_rest(n_paths, n_steps):
             assert d[k] == e[k]
 
 
-def test_fig1_grid_is_nested_on_one_shift():
+def test_fig1_grid_spans_1_to_365_on_one_shift():
     opts = workloads.fig1_options()
     assert len(opts) == 2 * len(workloads.FIG1_DATES)
     lsm = [o for o in opts if o.rule == workloads.RULE_LSM]
     assert [o.n_steps for o in lsm] == list(workloads.FIG1_DATES)
-    for a, b in zip(workloads.FIG1_DATES, workloads.FIG1_DATES[1:]):
+    assert set(range(1, 17)) <= set(workloads.FIG1_DATES) and workloads.FIG1_DATES[-1] == 365
+    assert all(b - a <= 8 for a, b in zip(workloads.FIG1_DATES, workloads.FIG1_DATES[1:]))
+    assert set(workloads.FIG1_NESTED) <= set(workloads.FIG1_DATES)
+    for a, b in zip(workloads.FIG1_NESTED, workloads.FIG1_NESTED[1:]):
         assert b % a == 0                                                 # every grid contains the coarser one
     assert len({(o.S0, o.K, o.r, o.sigma, o.T, o.seed, o.n_paths) for o in opts}) == 1

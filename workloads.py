@@ -18,8 +18,9 @@ Workloads:
                  parameters drawn as in batch_options
   greeks_options 1024 puts, seed 5, drawn as batch_options but with
                  2^18 paths and 100 dates
-  fig1_options   the Longstaff-Schwartz Table 1 put on nested power-of-two
-                 date grids, one shift seed, for LSM and the paper's rule
+  fig1_options   the Longstaff-Schwartz Table 1 put for m = 1..16, then
+                 every 8th m to 360 and m = 365 exercise dates, one shift
+                 seed, for LSM and the paper's rule
 A basis of size p spans {1, S, .., S^(p-1)}; the library and the oracle
 regress on powers of the moneyness y = S/K - 1, the same span.
 """
@@ -108,13 +109,17 @@ def scaled(opt, n_paths=None, n_steps=None):
     return Option(**d)
 
 
-FIG1_DATES = (1, 2, 4, 8, 16, 32, 64, 128, 256)
+# Fig. 1 grid: every m in 1..16, then every 8th m up to 360, and m = 365
+FIG1_DATES = tuple(range(1, 17)) + tuple(range(24, 361, 8)) + (365,)
+# the nested power-of-two grids within it (each contains the coarser ones)
+FIG1_NESTED = (1, 2, 4, 8, 16, 32, 64, 128, 256)
 
 
 def fig1_options(dates=FIG1_DATES, n_paths=2 ** 16, seed=21, rules=(RULE_LSM, RULE_PAPER_UB)):
     """Value vs number of exercise dates (the paper's Fig. 1, which prints no
     parameters): the Longstaff-Schwartz Table 1 put (S0 36, K 40, r 6 %,
-    sigma 20 %, T 1 year, basis 3) on the same shift seed for every m; the
-    power-of-two date grids are nested.  Ordered rule-major, then by m."""
+    sigma 20 %, T 1 year, basis 3) on the same shift seed for every m from
+    1 to 365 (FIG1_DATES); its power-of-two date grids (FIG1_NESTED) are
+    nested.  Ordered rule-major, then by m."""
     return [Option(36.0, 40.0, 0.06, 0.2, 1.0, m, n_paths, basis=3, type=PUT, seed=seed, rule=rule)
             for rule in rules for m in dates]
