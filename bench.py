@@ -719,6 +719,24 @@ def run_amc(args):
             return total, sum(gen) / steps, sum(swp) / steps, res
         return ev[0].elapsed_time(ev[1]), None, None, res
 
+    if args.profile_cluster:
+        # profiling mode: one batch-class option (2^18 paths, 252 dates, p = 4), its paths once,
+        # then only its cluster-sweep launches (for ncu)
+        copt = workloads.scaled(opt, n_paths=2 ** 18)
+        S = torch.empty((copt.n_steps, amc.amc_path_ld(copt.n_paths)), dtype=torch.float32, device="cuda")
+        res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            amc.amc_generate_paths(ctx, copt, amc.AMC_MIXED, S, stream=stream)
+            for _ in range(args.warmup + args.steps):
+                amc.amc_sweep(ctx, copt, amc.AMC_MIXED, S, res, stream=stream)
+            stream.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "cluster", "price": float(res[0].item()), "status": float(res[5].item())}),
+                  flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.profile_batch:
         bctx = amc.Context(local, arena_bytes=32 << 30)
         opts = workloads.batch_options()
@@ -943,6 +961,8 @@ def main():
                     help="run only the boundary valuation launches (for ncu captures)")
     ap.add_argument("--profile-paper", action="store_true",
                     help="run only the paper-rule sweeps (for ncu captures)")
+    ap.add_argument("--profile-cluster", action="store_true",
+                    help="only the cluster-sweep launches of one 2^18-path option (for ncu)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only the 4096-option batch, twice (for ncu launch lists)")
     ap.add_argument("--profile-large", action="store_true",
