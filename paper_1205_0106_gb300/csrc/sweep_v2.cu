@@ -298,30 +298,37 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // Gram pass of date d over the own paths: y in place, in-the-money
     // moments summed over the warp into sm.redG[buf][warp][k]
     auto gram_post = [&](int d, int buf) {
+        // the in-the-money indicator I = sat(-y 2^100) (put) or sat(y 2^100)
+        // (call) is exactly 1 for a nonzero FP32 y of the money's sign
+        // (|y| >= 2^-48) and 0 otherwise, so y I is the in-place value and I
+        // the count (multiplies instead of compares and selects); paths at
+        // or beyond nloc (last CTA) take 0 by selects
         float g[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) g[k] = 0.f;
         float *sl = sm.S[d % kSlots];
+        const float big = PUT ? -0x1p100f : 0x1p100f;
+        auto one = [&](float s, bool valid, float &yo) {
+            const float yr = fmaf(s, invK, -1.f);
+            const float in = valid ? __saturatef(yr * big) : 0.f;
+            const float y = valid ? yr * in : 0.f;
+            yo = y;
+            const float yy = y * y, y3 = yy * y;
+            g[0] += in;
+            g[1] += y;
+            g[2] += yy;
+            g[3] += y3;
+            g[4] = fmaf(yy, yy, g[4]);
+            g[5] = fmaf(yy, y3, g[5]);
+            g[6] = fmaf(y3, y3, g[6]);
+        };
 #pragma unroll
         for (int i = 0; i < kPPT; i += 2) {
             const int idx = pidx(i);
             const float2 s2 = *reinterpret_cast<const float2 *>(sl + idx);
             float2 y2;
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const float yr = fmaf(h2 ? s2.y : s2.x, invK, -1.f);
-                const bool itm = idx + h2 < nloc && (PUT ? yr < 0.f : yr > 0.f);
-                const float y = itm ? yr : 0.f;
-                (h2 ? y2.y : y2.x) = y;
-                const float yy = y * y, y3 = yy * y;
-                g[0] += itm ? 1.f : 0.f;
-                g[1] += y;
-                g[2] += yy;
-                g[3] += y3;
-                g[4] = fmaf(yy, yy, g[4]);
-                g[5] = fmaf(yy, y3, g[5]);
-                g[6] = fmaf(y3, y3, g[6]);
-            }
+            one(s2.x, idx < nloc, y2.x);
+            one(s2.y, idx + 1 < nloc, y2.y);
             *reinterpret_cast<float2 *>(sl + idx) = y2;
         }
         fence_proxy_async();             // these generic writes precede a later TMA refill
@@ -455,10 +462,15 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         stop = bar_work_any(sm.abort);                            // B1
         if (stop) break;
         if (w == 0 && j + 1 <= m - 1 && j + 1 - kSlots >= 1) issue(j + 1 - kSlots);   // slice j+1 consumed
-        // cross-CTA exchange: warp kXW0+k owns value slot k; it posts, runs
-        // its share of the next Gram pass (which also absorbs the other
-        // CTAs' lag), then gathers
-        const uint32_t tag = tag_hi | (uint32_t)j;
+        // cross-CTA exchange: warp kXW0+k owns value slot k; it posts the
+        // CTA's partial (an FP32 butterfly over the path warps' sums: few
+        // instructions, since the other warps start the Gram pass at the
+        // same time), runs its share of the next Gram pass (which also
+        // absorbs the other CTAs' lag), then gathers.  The right-hand sides
+        // are gathered from this exchange; the Gram moments one exchange
+        // later, from the units posted at the previous date, which are in
+        // place by then, so the barrier after the gather waits only for the
+        // right-hand sides (the solver warps still get one date to invert)
         const int xk = warp - kXW0;
         const bool xw = xk >= 0 && xk < kXV && ((mask >> xk) & 1u);
         uint64_t *xu = xch + ((size_t)j * kXV + (xw ? xk : 0)) * G;
@@ -466,13 +478,19 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             float pv = 0.f;
             if (xk < 7) pv = lane < 32 - kXW0 ? sm.redG[j & 1][kXW0 + lane][xk] : 0.f;
             else pv = lane < 32 - kXW0 ? sm.redR[kXW0 + lane][xk - 7] : 0.f;
-            dfl part = df_warp_sum(dfl{pv, 0.f});
+#pragma unroll
+            for (int off = 16; off; off >>= 1) pv += __shfl_xor_sync(kFull, pv, off);
             if (lane == 0 && inject_date != j)
-                st_unit(xu + lc, ((uint64_t)tag << 32) | __float_as_uint(__fadd_rn(part.hi, part.lo)));
+                st_unit(xu + lc, ((uint64_t)(tag_hi | (uint32_t)j) << 32) | __float_as_uint(pv));
         }
         // Gram pass of date j-3, posted at the next exchange
         if (j - 3 >= 1 && !sm.abort && wait_slice(j - 3)) gram_post(j - 3, (j - 1) & 1);
-        if (xw) {
+        // the Gram moments of date j-1, posted at exchange j+1
+        const bool gw = xk >= 0 && xk < nmom && j + 1 <= m + 1 && j - 1 >= 1;
+        if (xw && xk >= 7 || gw) {
+            const int jx = xk < 7 ? j + 1 : j;
+            const uint32_t tag = tag_hi | (uint32_t)jx;
+            uint64_t *xg = xch + ((size_t)jx * kXV + xk) * G;
             float vals[kMaxCtas / 32];
             const uint64_t t0 = globaltimer();
             for (;;) {
@@ -481,7 +499,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 for (int q = 0; q < kMaxCtas / 32; ++q) {
                     const int c = lane + 32 * q;
                     if (c < G) {
-                        const uint64_t u = ld_unit(xu + c);
+                        const uint64_t u = ld_unit(xg + c);
                         if ((uint32_t)(u >> 32) != tag) good = false;
                         vals[q] = __uint_as_float((uint32_t)u);
                     }
@@ -509,12 +527,12 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         }
         stop = bar_work_any(sm.abort);                            // B2
         if (stop) break;
-        if (hasG && warp == kXW0 + 1 && lane < 7) {               // Gram totals of date j-2 -> solver
-            const int b = (j - 2) % 3;
+        if (j + 1 <= m + 1 && j - 1 >= 1 && warp == kXW0 + 1 && lane < 7) {   // Gram totals of date j-1 -> solver
+            const int b = (j - 1) % 3;
             sm.gtot[b][lane] = (double)sm.tot_hi[lane] + (double)sm.tot_lo[lane];
             __syncwarp(0x7fu);
             __threadfence_block();
-            if (lane == 0) sm.gtot_date[b] = j - 2;
+            if (lane == 0) sm.gtot_date[b] = j - 1;
         }
         if (hasR) {
             // beta_j = Ginv_j R_j in double-float, in every path warp: lane
