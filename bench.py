@@ -230,6 +230,24 @@ def batch_and_greeks(amc, device, hbm, peak_kind, reps=2):
                                          "frac": gen_gbs / hbm, "peak_kind": peak_kind, "kernel": "pathgen_kernel",
                                          "launches": prof["gen_launches"], "ms": prof["gen_ms"]},
                     "s_with_profiling": dt_prof}
+    # the same batch with binary16 moneyness paths (AMC_MIXED16)
+    amc.amc_price_batch(bctx, opts, amc.AMC_MIXED16)
+    t = time.perf_counter()
+    for _ in range(reps):
+        res16 = amc.amc_price_batch(bctx, opts, amc.AMC_MIXED16)
+    dt16 = (time.perf_counter() - t) / reps
+    bctx.profile()
+    bctx.set_profiling(True)
+    amc.amc_price_batch(bctx, opts, amc.AMC_MIXED16)
+    prof16 = bctx.profile()
+    bctx.set_profiling(False)
+    sweep16_gbs = 2.0 * prof16["sweep_path_steps"] / (prof16["sweep_ms"] * 1e-3) / 1e9
+    out["batch"]["mixed16"] = {"s": dt16, "value": steps / dt16, "unit": METRIC,
+                               "failed": sum(r["status"] != 0 for r in res16),
+                               "sweep_ms": prof16["sweep_ms"], "gen_ms": prof16["gen_ms"],
+                               "roofline": {"bound": "hbm", "achieved": sweep16_gbs, "peak": hbm, "unit": "GB/s",
+                                            "frac": sweep16_gbs / hbm, "traffic": None, "peak_kind": peak_kind,
+                                            "algorithmic_bytes": 2.0 * prof16["sweep_path_steps"]}}
     gopts = workloads.greeks_options()
     gsteps = sum(o.path_steps for o in gopts)
     amc.amc_greeks(bctx, gopts, amc.AMC_MIXED)
@@ -478,10 +496,23 @@ def large_bench(amc, ctx, torch, stream, hbm, peak_kind, reps=3, warmup=1):
     nbytes = 16.0 * opt.n_paths * (opt.n_steps - 1)
     gbs = nbytes / (ms_sweep * 1e-3) / 1e9
     del S
+    # the same with the path array as binary16 moneyness: 12 B per path and date
+    Y = torch.empty((opt.n_steps, ld), dtype=torch.float16, device="cuda")
+    ms16 = timed(lambda: amc.amc_price_device(ctx, opt, amc.AMC_MIXED16, Y, res, stream=stream))
+    price16 = amc.res_to_dict(res.cpu().numpy())
+    ms16_sweep = timed(lambda: amc.amc_sweep(ctx, opt, amc.AMC_MIXED16, Y, res, stream=stream))
+    nbytes16 = 12.0 * opt.n_paths * (opt.n_steps - 1)
+    gbs16 = nbytes16 / (ms16_sweep * 1e-3) / 1e9
+    del Y
     return {"ms": ms, "value": units / (ms * 1e-3), "unit": METRIC, "price": price["price"],
             "std_err": price["std_err"], "sweep_ms": ms_sweep,
             "roofline_sweep": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes": nbytes},
+            "mixed16": {"ms": ms16, "value": units / (ms16 * 1e-3), "unit": METRIC, "price": price16["price"],
+                        "sweep_ms": ms16_sweep,
+                        "roofline_sweep": {"bound": "hbm", "achieved": gbs16, "peak": hbm, "unit": "GB/s",
+                                           "frac": gbs16 / hbm, "traffic": None, "peak_kind": peak_kind,
+                                           "algorithmic_bytes": nbytes16}},
             "workload": "put S0 100 K 100 r 0.05 sigma 0.3 T 1, 2^22 paths x 252 dates, basis 4, shift seed 2, "
                         "mixed: above the register-resident sweep's 1.17 M paths"}
 
@@ -682,7 +713,7 @@ def run_amc(args):
 
     def time_steps(prec, steps, warmup, split=False, streaming=False):
         # streaming: every sweep through the streaming design (context injection kind 3)
-        dt = torch.float64 if prec == amc.AMC_FP64 else torch.float32
+        dt = {amc.AMC_FP64: torch.float64, amc.AMC_MIXED16: torch.float16}.get(prec, torch.float32)
         S = torch.empty((opt.n_steps, ld), dtype=dt, device="cuda")
         res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
 
@@ -857,6 +888,12 @@ def run_amc(args):
     fs_ms, _, _, fsres = time_steps(amc.AMC_FP64, max(3, args.steps // 4), 2, streaming=True)
     fp64s_ms = fs_ms / max(3, args.steps // 4)
     fp64s_price = amc.res_to_dict(fsres.cpu().numpy())["price"]
+    # the path array as binary16 moneyness (AMC_MIXED16): whole pricings, then generate and sweep apart
+    h16_steps = max(3, args.steps // 2)
+    h16_ms, _, _, h16res = time_steps(amc.AMC_MIXED16, h16_steps, 2)
+    h16_ms /= h16_steps
+    _, h16_gen_ms, h16_sweep_ms, _ = time_steps(amc.AMC_MIXED16, h16_steps, 2, split=True)
+    h16_price = amc.res_to_dict(h16res.cpu().numpy())
 
     # end to end through the host API: option in, price out (host buffers)
     for _ in range(2):
@@ -895,6 +932,19 @@ def run_amc(args):
                                       units / (gen_ms * 1e-3)),
               "note": "issue-bound (ALU); the HBM write fraction is the secondary bound"}
     dominant = rl_gen if gen_ms >= sweep_ms else rl_sweep
+    h16_gbs_sweep = 2.0 * units / (h16_sweep_ms * 1e-3) / 1e9
+    h16_gbs_gen = 2.0 * units / (h16_gen_ms * 1e-3) / 1e9
+    mixed16 = {"value": units * ws / (h16_ms * 1e-3), "unit": METRIC, "ms_per_step": h16_ms,
+               "gen_ms": h16_gen_ms, "sweep_ms": h16_sweep_ms, "price": h16_price["price"],
+               "std_err": h16_price["std_err"], "err_vs_oracle_over_K": None,
+               "path_bytes": 2.0 * units, "path_bytes_mixed": 4.0 * units,
+               "roofline_sweep": {"bound": "hbm", "achieved": h16_gbs_sweep, "peak": hbm, "unit": "GB/s",
+                                  "frac": h16_gbs_sweep / hbm, "traffic": None, "peak_kind": peak_kind,
+                                  "kernel": "sweep_lsm_v2_kernel (binary16 ring)", "algorithmic_bytes": 2.0 * units},
+               "roofline_pathgen": {"bound": "hbm", "achieved": h16_gbs_gen, "peak": hbm, "unit": "GB/s",
+                                    "frac": h16_gbs_gen / hbm, "traffic": None, "peak_kind": peak_kind,
+                                    "kernel": "pathgen_kernel (binary16 store)", "algorithmic_bytes": 2.0 * units},
+               "storage": "y = S/K - 1 in IEEE binary16, 2 B per path-step (AMC_MIXED16)"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -910,7 +960,7 @@ def run_amc(args):
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 64},
             "gpu_launches": 3 * args.steps,
             "roofline": dominant, "roofline_sweep": rl_sweep, "roofline_pathgen": rl_gen,
-            "clocks": ck}
+            "mixed16": mixed16, "clocks": ck}
     if not args.no_oos:
         line["oos"] = oos_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
         line["paper_rule"] = paper_rule_bench(amc, ctx, torch, stream, opt, hbm, peak_kind)
@@ -940,6 +990,7 @@ def run_amc(args):
         line["cpu_baseline"], ref_price = cpu_baseline(opt)
         if ref_price is not None:
             line["err_vs_oracle_over_K"] = abs(price["price"] - ref_price) / opt.K
+            line["mixed16"]["err_vs_oracle_over_K"] = abs(h16_price["price"] - ref_price) / opt.K
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

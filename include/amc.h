@@ -65,7 +65,18 @@ enum { AMC_RULE_LSM = 0, AMC_RULE_PAPER_UB = 1, AMC_RULE_EUROPEAN = 2 };
  * exercise decisions near the fitted boundary flip under perturbations of
  * order 1e-7 and the FP64 estimate itself moves by more than 2e-4 K under
  * FP32-level noise; price such options with AMC_FP64 (or a smaller basis).  */
-enum { AMC_FP64 = 0, AMC_MIXED = 1 };
+/* AMC_MIXED16 is AMC_MIXED with the path array stored as the moneyness
+ * y = S/K - 1 in IEEE binary16 (round to nearest even) instead of S in
+ * FP32: half the bytes of S, and the sweeps read y as stored.  The
+ * paths it stores are those of AMC_MIXED rounded to binary16 (a relative
+ * step of 2^-11 in y).  Accepted by amc_generate_paths, amc_sweep and
+ * amc_fit_boundary (the LSM rule, no Greeks), amc_price_american and
+ * amc_price_device (LSM), and amc_price_batch and amc_price_batch_device
+ * (every option LSM); AMC_EINVAL everywhere else.  The rounding moves the
+ * estimate by far less than 2e-4 K on options where LSM is stable at FP32
+ * precision (3e-5 K on the 252-date put); on the unstable kind above it
+ * moves by up to several 1e-4 K.                                           */
+enum { AMC_FP64 = 0, AMC_MIXED = 1, AMC_MIXED16 = 2 };
 
 /* One option.  72 bytes, naturally aligned.                                */
 typedef struct amc_option {
@@ -154,7 +165,8 @@ int amc_validate_option(const amc_option *opt);
 /* Row stride (elements) of the date-major path array S[m][ld]: n_paths
  * rounded up to a multiple of 32.                                          */
 int64_t amc_path_ld(int64_t n_paths);
-/* Bytes of S for one option: n_steps * ld * (8 for AMC_FP64, 4 otherwise). */
+/* Bytes of S for one option: n_steps * ld * (8 for AMC_FP64, 4 for
+ * AMC_MIXED, 2 for AMC_MIXED16).                                           */
 size_t amc_path_bytes(int n_steps, int64_t n_paths, int prec);
 /* Digital shifts: out[d] = high 32 bits of the d-th SplitMix64 output.     */
 int amc_digital_shifts(uint64_t seed, int n_dims, uint32_t *out);
@@ -178,7 +190,8 @@ int amc_sobol(amc_ctx *ctx, int n_dims, int64_t n_points, uint64_t seed,
               uint32_t *x_dev, int64_t ld, void *stream);
 /* Steps 1-3: paths S[j-1][i] = S_i(t_j), date-major, row stride ld >=
  * amc_path_ld(n_paths) and a multiple of 32; S 16-byte aligned (else
- * AMC_EINVAL); float for AMC_MIXED, double for AMC_FP64.  Entries
+ * AMC_EINVAL); float for AMC_MIXED, double for AMC_FP64, and for
+ * AMC_MIXED16 the binary16 moneyness S_i(t_j)/K - 1 (uint16 bits).  Entries
  * n_paths <= i < ld of a row may receive the values of the extra Sobol'
  * points; nothing beyond ld is written.                                    */
 int amc_generate_paths(amc_ctx *ctx, const amc_option *opt, int prec,

@@ -21,7 +21,7 @@ AMC_OK, AMC_EINVAL, AMC_ENOMEM, AMC_ECUDA, AMC_ETIMEOUT, AMC_EBUSY, AMC_PENDING,
 AMC_ECANCELED = -8
 AMC_PUT, AMC_CALL = 0, 1
 AMC_RULE_LSM, AMC_RULE_PAPER_UB, AMC_RULE_EUROPEAN = 0, 1, 2
-AMC_FP64, AMC_MIXED = 0, 1
+AMC_FP64, AMC_MIXED, AMC_MIXED16 = 0, 1, 2
 AMC_RES_DOUBLES = 8
 AMC_COEF_STRIDE = 5
 AMC_DUAL_MAX_WORK = 1 << 40

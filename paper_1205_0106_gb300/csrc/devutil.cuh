@@ -72,6 +72,52 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
     return d;
 }
 
+// IEEE binary16 storage: two values in one 32-bit word, the element at the
+// lower address in the low half.  Widening is exact; narrowing rounds to
+// nearest even.
+__device__ __forceinline__ float h_to_f(uint16_t h) {
+    float f;
+    asm("{.reg .b16 t;\n\tmov.b16 t, %1;\n\tcvt.f32.f16 %0, t;}" : "=f"(f) : "h"(h));
+    return f;
+}
+__device__ __forceinline__ f2 h2_to_f2(uint32_t w) {
+    float lo, hi;
+    asm("{.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\tcvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(w));
+    return f2_pack(lo, hi);
+}
+__device__ __forceinline__ uint32_t f_to_h2(float lo, float hi) {
+    uint32_t w;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));   // first operand -> upper half
+    return w;
+}
+
+// One date slice of the path array in shared memory, as the mixed LSM
+// sweeps hold it: FP32 prices S, or binary16 moneyness y = S/K - 1.  The
+// Gram pass of a date rewrites the slice in place as y for in-the-money
+// paths and 0 otherwise; the raw_* reads come before that pass, the y*
+// reads after it.  A binary16 slice takes the rewritten values exactly
+// (each is a stored value or 0).
+__device__ __forceinline__ float raw_y(const float *sl, int i, float invK) { return fmaf(sl[i], invK, -1.f); }
+__device__ __forceinline__ float raw_y(const uint16_t *sl, int i, float) { return h_to_f(sl[i]); }
+__device__ __forceinline__ f2 raw_y2(const float *sl, int i, float invK) {
+    return f2_fma(*reinterpret_cast<const f2 *>(sl + i), f2_splat(invK), f2_splat(-1.f));
+}
+__device__ __forceinline__ f2 raw_y2(const uint16_t *sl, int i, float) {
+    return h2_to_f2(*reinterpret_cast<const uint32_t *>(sl + i));
+}
+__device__ __forceinline__ float y_at(const float *sl, int i) { return sl[i]; }
+__device__ __forceinline__ float y_at(const uint16_t *sl, int i) { return h_to_f(sl[i]); }
+__device__ __forceinline__ f2 y2_at(const float *sl, int i) { return *reinterpret_cast<const f2 *>(sl + i); }
+__device__ __forceinline__ f2 y2_at(const uint16_t *sl, int i) {
+    return h2_to_f2(*reinterpret_cast<const uint32_t *>(sl + i));
+}
+__device__ __forceinline__ void put_y2(float *sl, int i, f2 v) { *reinterpret_cast<f2 *>(sl + i) = v; }
+__device__ __forceinline__ void put_y2(uint16_t *sl, int i, f2 v) {
+    *reinterpret_cast<uint32_t *>(sl + i) = f_to_h2(f2_lo(v), f2_hi(v));
+}
+
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

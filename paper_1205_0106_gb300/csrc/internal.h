@@ -130,6 +130,7 @@ struct KArgs {
     int32_t max_m;
     int32_t max_slots;              // largest bridge stack over the jobs (path generation)
     int32_t jobs_type;              // AMC_PUT / AMC_CALL shared by all jobs of a mixed LSM launch
+    int32_t h16;                    // path arrays hold binary16 moneyness (AMC_MIXED16)
     int64_t total;                  // path-generation tiles over all jobs
     const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
     uint64_t timeout_ns;
@@ -147,7 +148,9 @@ cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t
 // (pathgen.cu): the rules that need no regression across paths, and the
 // valuation of a fitted boundary.  One option (a.one); per-CTA sums into
 // a.one.fin[grid][4] for launch_finalize.
-enum { kStore = 0, kPaperRule = 1, kEuropean = 2, kBoundary = 3 };
+// kStore16 (FP32 only) stores the moneyness y = S/K - 1 in binary16
+// instead of S (AMC_MIXED16).
+enum { kStore = 0, kPaperRule = 1, kEuropean = 2, kBoundary = 3, kStore16 = 4 };
 cudaError_t pathgen_fused_grid(const KArgs &a, int mode, bool fp64, int sm_count, int64_t *grid);
 cudaError_t launch_pathgen_fused(const KArgs &a, int mode, bool fp64, int64_t grid, cudaStream_t st);
 cudaError_t launch_sweep_lsm(const KArgs &a, int total_ctas, int chunks, bool fp64, bool greeks,
@@ -204,9 +207,10 @@ struct StreamArgs {
     int32_t *deg;                   // [m] degenerate flags
     int32_t *ndeg;                  // degenerate dates so far
     int32_t grid;                   // CTAs of every pass
+    int32_t h16;                    // S holds binary16 moneyness (AMC_MIXED16)
 };
 constexpr int kStreamThreads = 256;
-int64_t stream_grid(int sm_count, bool fp64, bool put);
+int64_t stream_grid(int sm_count, bool fp64, bool put, bool h16 = false);
 cudaError_t launch_lsm_stream(const StreamArgs &a, bool fp64, cudaStream_t st);
 
 // Dual upper bound of a fitted boundary (dual.cu): the option, its outer

@@ -91,10 +91,11 @@ struct alignas(4 * sizeof(Real)) R4 {
 
 // The 4 points of one bridge node: z = N^{-1}(u) of the Sobol' integers xq,
 // W = wl W_left + wr W_right + sd z (ref. [13]), S = S0 exp(drift + sig W)
-// (Eq. 9 in log space; base 2 in FP32).
+// + off (Eq. 9 in log space; base 2 in FP32).  off = 0 gives S; S0 / K for
+// S0 and off = -1 give the moneyness y = S/K - 1 with one rounding.
 template <bool FP64, typename Real>
 __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Real wr, Real sd, Real drift,
-                                            Real sig, Real S0, const R4<Real> &Wl, const R4<Real> &Wr,
+                                            Real sig, Real S0, Real off, const R4<Real> &Wl, const R4<Real> &Wr,
                                             R4<Real> &Wo, R4<Real> &So) {
     if (FP64) {
         Real z[4];
@@ -104,7 +105,7 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
         for (int q = 0; q < 4; ++q) {
             const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
             Wo.v[q] = W;
-            So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
+            So.v[q] = fma(S0, (Real)exp((double)fma(sig, W, drift)), off);
         }
     } else {
         // points (0, 1) and (2, 3) as packed pairs: central-region
@@ -137,7 +138,8 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
                                        f2_mul(f2_splat((float)wl),
                                               f2_pack((float)Wl.v[2 * h], (float)Wl.v[2 * h + 1]))));
             const f2 e = f2_fma(f2_splat((float)sig), W, f2_splat((float)drift));
-            const f2 Sv = f2_mul(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))));
+            const f2 Sv = f2_fma(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))),
+                                 f2_splat((float)off));
             Wo.v[2 * h] = (Real)f2_lo(W);
             Wo.v[2 * h + 1] = (Real)f2_hi(W);
             So.v[2 * h] = (Real)f2_lo(Sv);
@@ -150,7 +152,9 @@ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 constexpr int kGB = ilog2(kTilePoints) - 1;       // Gray bits 1..kGB of the thread's point offset 4t
 static_assert((1 << ilog2(kTilePoints)) == kTilePoints && kGB + 1 < 12, "tile of 2^k points, direction numbers v_1..v_12");
 
-// MODE kStore writes the path array (steps 1-3).  The other modes value
+// MODE kStore writes the path array (steps 1-3); kStore16 writes it as
+// binary16 moneyness y = S/K - 1 (8 bytes per thread and date).  The other
+// modes value
 // every path as its dates are formed and store nothing; they need no
 // regression across paths, and their per-path value does not depend on the
 // order in which the bridge forms the dates:
@@ -170,6 +174,8 @@ template <bool FP64, int MODE>
 __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_constant__ KArgs a) {
     using Real = typename PG<FP64>::Real;
     using Node = typename PG<FP64>::Node;
+    constexpr bool STORE = MODE == kStore || MODE == kStore16;
+    static_assert(!(FP64 && MODE == kStore16), "binary16 moneyness is an FP32-path format");
     extern __shared__ __align__(32) unsigned char smem[];
     const int max_m = a.max_m;
     const PathgenSmem L = pathgen_layout(max_m, a.max_slots, FP64, MODE);
@@ -237,7 +243,8 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + t4;
         const double mu = J.r - 0.5 * J.sigma * J.sigma;
         const Real sqdt = (Real)sqrt(J.dt);
-        const Real S0 = (Real)J.S0;
+        const Real S0 = MODE == kStore16 ? (Real)(J.S0 * J.invK) : (Real)J.S0;
+        const Real off = MODE == kStore16 ? Real(-1) : Real(0);
         // exponent per node: FP32 in base 2 (ex2), FP64 in base e
         const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
         const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
 
         // FP32 store/paper-rule modes unrolled: later nodes' quantiles overlap earlier nodes' bridge and store
         // (0.442 -> 0.405 ms on 2^20 x 252); FP64 stays rolled (unrolled by 8: 69 -> 106 ms all-FP64 pricing)
-#pragma unroll ((!FP64 && (MODE == kStore || MODE == kPaperRule)) ? 8 : 1)
+#pragma unroll ((!FP64 && (STORE || MODE == kPaperRule)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
             const Node nd = s_nodes[n];
             const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];
@@ -280,9 +287,15 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
             const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
             R4<Real> Wo, So;
-            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
+            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, off, Wl, Wr, Wo, So);
             s_W[nd.so * kPathgenThreads + tid] = Wo;
-            if (MODE == kStore) {
+            if (MODE == kStore16) {
+                if (store) {
+                    uint16_t *dst = reinterpret_cast<uint16_t *>(J.S) + base + t4 + (int64_t)(nd.date - 1) * ld;
+                    *reinterpret_cast<uint2 *>(dst) = make_uint2(dev::f_to_h2((float)So.v[0], (float)So.v[1]),
+                                                                 dev::f_to_h2((float)So.v[2], (float)So.v[3]));
+                }
+            } else if (MODE == kStore) {
                 if (store) {
                     Real *dst = S + (int64_t)(nd.date - 1) * ld;
                     if (FP64) {                                           // two 16-byte stores
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
                 }
             }
         }
-        if (MODE != kStore) {
+        if (!STORE) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if ((int64_t)base + t4 + q >= J.N) continue;
@@ -346,7 +359,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             }
         }
     }
-    if (MODE != kStore) {
+    if (!STORE) {
         // fixed-order CTA sum into this CTA's slot of J.fin (finalize_kernel)
         __shared__ double red[kPathgenThreads / 32][2];
 #pragma unroll
@@ -447,7 +460,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
             const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
             const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
             R4<Real> Wo, So;
-            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
+            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Real(0), Wl, Wr, Wo, So);
             s_W[nd.so * kPathgenThreads + tid] = Wo;
             if (store) {
                 Real *dst = S + (int64_t)(nd.date - 1) * ld;
@@ -508,6 +521,7 @@ PathgenFn pathgen_fn(int mode, bool fp64) {
         case kPaperRule: return fp64 ? pathgen_kernel<true, kPaperRule> : pathgen_kernel<false, kPaperRule>;
         case kEuropean: return fp64 ? pathgen_kernel<true, kEuropean> : pathgen_kernel<false, kEuropean>;
         case kBoundary: return fp64 ? pathgen_kernel<true, kBoundary> : pathgen_kernel<false, kBoundary>;
+        case kStore16: return pathgen_kernel<false, kStore16>;
         default: return fp64 ? pathgen_kernel<true, kStore> : pathgen_kernel<false, kStore>;
     }
 }
@@ -535,7 +549,8 @@ cudaError_t launch_pathgen(const KArgs &a, bool fp64, int sm_count, cudaStream_t
     PathgenFn kern;
     size_t smem;
     int64_t grid;
-    cudaError_t e = pathgen_setup(a, kStore, fp64, sm_count, &kern, &smem, &grid);
+    if (a.h16 && fp64) return cudaErrorInvalidValue;
+    cudaError_t e = pathgen_setup(a, a.h16 ? kStore16 : kStore, fp64, sm_count, &kern, &smem, &grid);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, kPathgenThreads, smem, st>>>(a);
     return cudaGetLastError();
@@ -550,7 +565,8 @@ cudaError_t pathgen_fused_grid(const KArgs &a, int mode, bool fp64, int sm_count
 }
 
 cudaError_t launch_pathgen_fused(const KArgs &a, int mode, bool fp64, int64_t grid, cudaStream_t st) {
-    if (a.total <= 0 || grid <= 0 || a.jobs != nullptr || mode == kStore) return cudaErrorInvalidValue;
+    if (a.total <= 0 || grid <= 0 || a.jobs != nullptr || mode == kStore || mode == kStore16)
+        return cudaErrorInvalidValue;
     PathgenFn kern;
     size_t smem;
     int64_t g;

@@ -143,7 +143,13 @@ int grow_scratch(double **buf, int64_t *have, int64_t need, size_t per) {
     return AMC_OK;
 }
 
-int check_prec(int prec) { return (prec == AMC_FP64 || prec == AMC_MIXED) ? AMC_OK : AMC_EINVAL; }
+// AMC_MIXED16 only where the caller allows it (the LSM sweeps and path
+// generation into a caller array).
+int check_prec(int prec, bool h16_ok = false) {
+    if (prec == AMC_FP64 || prec == AMC_MIXED) return AMC_OK;
+    return (prec == AMC_MIXED16 && h16_ok) ? AMC_OK : AMC_EINVAL;
+}
+size_t elem_bytes(int prec) { return prec == AMC_FP64 ? 8 : (prec == AMC_MIXED16 ? 2 : 4); }
 
 // Caller path storage: rows must start on 16-byte boundaries for the
 // vector loads and stores, so S must be 16-byte aligned and ld a multiple
@@ -155,7 +161,7 @@ int check_storage(const void *S, int64_t ld, int64_t n_paths) {
 
 int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, cudaStream_t st) {
     AMC_TRY(host_validate(o));
-    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_prec(prec, true));
     AMC_TRY(check_storage(S, ld, o->n_paths));
     DevBridge *b;
     AMC_TRY(get_bridge(c, o->n_steps, &b));
@@ -176,6 +182,7 @@ int do_generate(amc_ctx *c, const amc_option *o, int prec, void *S, int64_t ld, 
     a.max_slots = b->nslots;
     a.total = J.n_tiles;
     a.V = c->V;
+    a.h16 = prec == AMC_MIXED16 ? 1 : 0;
     cudaEvent_t pe = prof_begin(c, st);
     AMC_TRY_CUDA(launch_pathgen(a, prec == AMC_FP64, c->sm_count, st));
     prof_end(c, pe, 0, o->n_paths * (int64_t)o->n_steps, st);
@@ -221,7 +228,8 @@ int do_sweep_stream(amc_ctx *c, const amc_option *o, int prec, const void *S, in
     J.res = res;
     J.status = c->status1;
     J.coef = coef;
-    const int64_t grid = stream_grid(c->sm_count, fp64, o->type == AMC_PUT);
+    sa.h16 = prec == AMC_MIXED16 ? 1 : 0;
+    const int64_t grid = stream_grid(c->sm_count, fp64, o->type == AMC_PUT, sa.h16 != 0);
     // cash flows [ld] (up to 8 bytes each), partials [grid][kNV], coefficients
     // [AMC_MAX_STEPS][4], then degenerate flags and count (int32, in doubles)
     const int64_t n_flags = (AMC_MAX_STEPS + 2) / 2;
@@ -249,7 +257,7 @@ int do_sweep_stream(amc_ctx *c, const amc_option *o, int prec, const void *S, in
 int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t ld, bool greeks, double *res,
              cudaStream_t st, double *coef = nullptr) {
     AMC_TRY(host_validate(o));
-    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_prec(prec, o->rule == AMC_RULE_LSM && !greeks));
     AMC_TRY(check_storage(S, ld, o->n_paths));
     if (!res || ((uintptr_t)res & 7u) != 0) return AMC_EINVAL;
     if (greeks && o->rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
@@ -298,6 +306,8 @@ int do_sweep(amc_ctx *c, const amc_option *o, int prec, const void *S, int64_t l
     a.n_jobs = 1;
     a.max_m = o->n_steps;
     a.V = c->V;
+    a.h16 = prec == AMC_MIXED16 ? 1 : 0;
+    if (a.h16 && pl.kind < 2) return AMC_EINVAL;      // the binary16 format is read by the mixed LSM sweeps only
     if (pl.kind == 1 && o->rule == AMC_RULE_LSM)
         AMC_TRY_CUDA(cudaMemsetAsync(c->arrive1, 0, sizeof(uint32_t) * o->n_steps, st));
     AMC_TRY_CUDA(cudaMemsetAsync(c->status1, 0, sizeof(int32_t), st));
@@ -434,13 +444,14 @@ amc_option make_option(double S0, double K, double r, double sigma, double T, in
 // synchronisation.
 int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, amc_result *out,
               const DeviceIO *dev = nullptr, cudaStream_t user_st = nullptr) {
-    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_prec(prec, !greeks));
     for (int i = 0; i < n; ++i) {
         amc_option o = opts[i];
         if (dev && dev->S0) o.S0 = 1.0;             // checked on the device
         if (dev && dev->sigma) o.sigma = 0.2;
         AMC_TRY(host_validate(&o));
         if (greeks && opts[i].rule == AMC_RULE_PAPER_UB) return AMC_EINVAL;
+        if (prec == AMC_MIXED16 && opts[i].rule != AMC_RULE_LSM) return AMC_EINVAL;
     }
     struct Item {
         int idx;
@@ -623,7 +634,7 @@ int group_cta_cap(amc_ctx *c, const SweepPlan &pl) {
 }
 
 size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec) {
-    const size_t esz = prec == AMC_FP64 ? 8 : 4;
+    const size_t esz = elem_bytes(prec);
     size_t need = align_up((size_t)o.n_steps * host_ld(o.n_paths) * esz, 256);            // paths
     need += pl.kind == 3 ? 0                                                              // on-chip exchange
             : pl.kind == 2 ? align_up(v2_xch_units(o.n_steps, pl.ctas) * 8, 256)          // exchange units
@@ -636,7 +647,7 @@ size_t option_bytes(const amc_option &o, const SweepPlan &pl, int prec) {
 int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *plans, int nw, int prec, bool greeks,
                  SubArena &ar, cudaStream_t st, double **res_out, const DeviceIO *io) {
     const bool fp64 = prec == AMC_FP64;
-    const size_t esz = fp64 ? 8 : 4;
+    const size_t esz = elem_bytes(prec);
     const SweepPlan plan0 = plans[0];
     const bool lsm = opts[0]->rule == AMC_RULE_LSM;
     std::vector<Job> jobs(nw);
@@ -726,6 +737,8 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     a.jobs_type = opts[0]->type;
     a.total = tiles;
     a.V = c->V;
+    a.h16 = prec == AMC_MIXED16 ? 1 : 0;
+    if (a.h16 && plan0.kind < 2) return AMC_EINVAL;
     int64_t units = 0;
     for (int k = 0; k < nw; ++k) units += opts[k]->n_paths * (int64_t)opts[k]->n_steps;
     cudaEvent_t pe = prof_begin(c, st);
@@ -763,7 +776,7 @@ int amc_validate_option(const amc_option *opt) { return host_validate(opt); }
 int64_t amc_path_ld(int64_t n_paths) { return n_paths < 1 ? 0 : host_ld(n_paths); }
 size_t amc_path_bytes(int n_steps, int64_t n_paths, int prec) {
     if (n_steps < 1 || n_paths < 1) return 0;
-    return (size_t)n_steps * host_ld(n_paths) * (prec == AMC_FP64 ? 8 : 4);
+    return (size_t)n_steps * host_ld(n_paths) * elem_bytes(prec);
 }
 int amc_digital_shifts(uint64_t seed, int n_dims, uint32_t *out) {
     if (n_dims < 0 || (n_dims > 0 && !out)) return AMC_EINVAL;
@@ -1117,12 +1130,12 @@ int amc_price_american(amc_ctx *c, double S0, double K, double r, double sigma, 
     if (!c || !out) return AMC_EINVAL;
     amc_option o = make_option(S0, K, r, sigma, T, n_steps, n_paths, basis, type, seed, rule);
     AMC_TRY(host_validate(&o));
-    AMC_TRY(check_prec(prec));
+    AMC_TRY(check_prec(prec, rule == AMC_RULE_LSM));
     AMC_TRY_CUDA(cudaSetDevice(c->device));
     c->arena_top = 0;
     const int64_t ld = host_ld(n_paths);
     void *S;
-    AMC_TRY(arena_alloc(c, (size_t)n_steps * ld * (prec == AMC_FP64 ? 8 : 4), &S));
+    AMC_TRY(arena_alloc(c, (size_t)n_steps * ld * elem_bytes(prec), &S));
     cudaStream_t st = c->stream;
     AMC_TRY_CUDA(cudaEventRecord(c->ev[0], st));
     AMC_TRY(do_generate(c, &o, prec, S, ld, st));

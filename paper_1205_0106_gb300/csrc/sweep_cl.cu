@@ -15,8 +15,8 @@
 // paths per thread with the cash flow (units of K) in registers, plus one
 // path each for the first 512 of them with its cash flow in shared memory;
 // warp 0 owns none and solves.  The date slices of S stream through a ring
-// of 3 slots of 64 KB in shared memory, filled by TMA bulk copies about one
-// date ahead.  Per date d (from m-1 down to 1), path warps:
+// of 3 slots in shared memory (64 KB each; 32 KB when the path array holds
+// binary16 moneyness), filled by TMA bulk copies about one date ahead.  Per date d (from m-1 down to 1), path warps:
 //   1. wait for beta_{d+1} (named barrier, published by the solver warp);
 //      exercise at d+1, discount, right-hand sides R_d of date d over their
 //      own paths (packed f32x2);
@@ -37,6 +37,8 @@
 // barrier, so no CTA leaves while a peer may write into its shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "devutil.cuh"
 #include "internal.h"
@@ -59,8 +61,10 @@ constexpr int kRegPaths = kPathThreads * kPPT; // 15872 paths in registers
 constexpr unsigned kFull = 0xffffffffu;
 static_assert(kPPC - kRegPaths <= kPathThreads, "one shared-memory path per path thread at most");
 
+// E: float (FP32 prices) or uint16_t (binary16 moneyness, AMC_MIXED16)
+template <typename E>
 struct SmemCl {
-    float S[kSlots][kPPC];
+    E S[kSlots][kPPC];
     uint64_t mbar[kSlots];                     // ring slots (TMA)
     uint64_t xbarR[2];                         // exchange arrivals of the right-hand sides, by date mod 2
     uint64_t xbarM[3];                         // and of the Gram moments, by date mod 3
@@ -267,21 +271,22 @@ __device__ __noinline__ dfl cl_gram_inverse(dfl Mq, int p, int lane, bool &deg) 
     return in ? xn : df_of(0.f);
 }
 
-template <bool PUT>
+template <bool PUT, bool H16>
 __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__ KArgs a) {
+    using E = typename std::conditional<H16, uint16_t, float>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemCl &sm = *reinterpret_cast<SmemCl *>(smem_raw);
+    SmemCl<E> &sm = *reinterpret_cast<SmemCl<E> *>(smem_raw);
     const int G = (int)cluster_size(), lc = (int)cluster_rank();
     const int jb = a.jobs ? (int)(blockIdx.x / (unsigned)G) : 0;
     const Job &J = a.jobs ? a.jobs[jb] : a.one;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = J.m, p = J.p;
     const float invK = (float)J.invK, disc = (float)J.disc;
-    const float *__restrict__ S = reinterpret_cast<const float *>(J.S);
+    const E *__restrict__ S = reinterpret_cast<const E *>(J.S);
     const int64_t N = J.N, ld = J.ld;
     const int64_t base = (int64_t)lc * kPPC;
     const int64_t rem = ld - base;
-    const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * 4u;
+    const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * (uint32_t)sizeof(E);
     const int nloc = (N - base) < kPPC ? (int)(N - base) : kPPC;
     int32_t *const status = J.status;
     const uint64_t timeout_ns = a.timeout_ns;
@@ -414,16 +419,16 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
         float cf[kPPT];
         bool stop = !wait_bar(&sm.mbar[m % kSlots], slot_parity(m), false);
         if (!stop) {
-            const float *sl = sm.S[m % kSlots];
+            const E *sl = sm.S[m % kSlots];
 #pragma unroll
             for (int i = 0; i < kPPT; ++i) {
                 const int idx = pidx(i);
-                const float y = fmaf(sl[idx], invK, -1.f);
+                const float y = raw_y(sl, idx, invK);
                 const float h = PUT ? -y : y;
                 cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
             }
             if (has_x) {
-                const float y = fmaf(sl[xidx], invK, -1.f);
+                const float y = raw_y(sl, xidx, invK);
                 const float h = PUT ? -y : y;
                 sm.cfx[t] = (xidx < nloc && h > 0.f) ? h : 0.f;
             }
@@ -437,12 +442,12 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
         // instead of compares and selects)
         auto gram = [&](int e) -> bool {
             if (!wait_bar(&sm.mbar[e % kSlots], slot_parity(e), false)) return false;
-            float *sl = sm.S[e % kSlots];
-            const f2 z2 = f2_splat(0.f), IK = f2_splat(invK), M1 = f2_splat(-1.f);
+            E *sl = sm.S[e % kSlots];
+            const f2 z2 = f2_splat(0.f);
             const float big = PUT ? -0x1p100f : 0x1p100f;
             f2 g0 = z2, g1 = z2, g2 = z2, g3 = z2, g4 = z2, g5 = z2, g6 = z2;
             auto pair = [&](int idx, bool tail) {
-                const f2 Yr = f2_fma(*reinterpret_cast<const f2 *>(sl + idx), IK, M1);
+                const f2 Yr = raw_y2(sl, idx, invK);
                 float ilo = __saturatef(f2_lo(Yr) * big), ihi = __saturatef(f2_hi(Yr) * big);
                 f2 Y;
                 if (tail) {
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                     Y = f2_mul(Yr, f2_pack(ilo, ihi));
                 }
                 const f2 I = f2_pack(ilo, ihi);
-                *reinterpret_cast<f2 *>(sl + idx) = Y;
+                put_y2(sl, idx, Y);
                 g0 = f2_add(g0, I);
                 const f2 YY = f2_mul(Y, Y), Y3 = f2_mul(YY, Y);
                 g1 = f2_add(g1, Y);
@@ -517,21 +522,21 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 const float b0 = sm.beta[pe][0], b1 = sm.beta[pe][1], b2 = sm.beta[pe][2], b3 = sm.beta[pe][3];
                 const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
                 const f2 DISC = f2_splat(disc), z2 = f2_splat(0.f), SG = f2_splat(PUT ? -1.f : 1.f);
-                const float *se = sm.S[(d + 1) % kSlots];
-                const float *sr = sm.S[d % kSlots];
+                const E *se = sm.S[(d + 1) % kSlots];
+                const E *sr = sm.S[d % kSlots];
                 f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
 #pragma unroll
                 for (int i = 0; i < kPPT; i += 2) {
                     const int idx = pidx(i);
                     if (ex) {
-                        const f2 Y = *reinterpret_cast<const f2 *>(se + idx);
+                        const f2 Y = y2_at(se, idx);
                         const f2 C = f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0);
                         const f2 H = f2_mul(Y, SG);
                         const float hl = f2_lo(H), hh = f2_hi(H);
                         cf[i] = hl > fmaxf(f2_lo(C), 0.f) ? hl : cf[i];
                         cf[i + 1] = hh > fmaxf(f2_hi(C), 0.f) ? hh : cf[i + 1];
                     }
-                    const f2 Y = *reinterpret_cast<const f2 *>(sr + idx);
+                    const f2 Y = y2_at(sr, idx);
                     const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
                     cf[i] = f2_lo(C);
                     cf[i + 1] = f2_hi(C);
@@ -547,14 +552,14 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 if (has_x) {                                          // the shared-memory path
                     float c = sm.cfx[t];
                     if (ex) {
-                        const float y = se[xidx];
+                        const float y = y_at(se, xidx);
                         const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
                         const float h = PUT ? -y : y;
                         c = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : c;
                     }
                     c *= disc;
                     sm.cfx[t] = c;
-                    const float y = sr[xidx];
+                    const float y = y_at(sr, xidx);
                     const float cc = y != 0.f ? c : 0.f, yy = y * y;
                     rr[0] += cc;
                     rr[1] = fmaf(c, y, rr[1]);
@@ -593,16 +598,16 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 stop = true;
             } else if (!sm.deg[1]) {
                 const float b0 = sm.beta[1][0], b1 = sm.beta[1][1], b2 = sm.beta[1][2], b3 = sm.beta[1][3];
-                const float *se = sm.S[1 % kSlots];
+                const E *se = sm.S[1 % kSlots];
 #pragma unroll
                 for (int i = 0; i < kPPT; ++i) {
-                    const float y = se[pidx(i)];
+                    const float y = y_at(se, pidx(i));
                     const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
                     const float h = PUT ? -y : y;
                     cf[i] = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : cf[i];
                 }
                 if (has_x) {
-                    const float y = se[xidx];
+                    const float y = y_at(se, xidx);
                     const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
                     const float h = PUT ? -y : y;
                     if ((PUT ? y < 0.f : y > 0.f) && h > cont) sm.cfx[t] = h;
@@ -663,13 +668,15 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
 
 }  // namespace
 
-size_t sweep_cl_smem() { return sizeof(SmemCl); }
+size_t sweep_cl_smem() { return sizeof(SmemCl<float>); }
 
 cudaError_t launch_sweep_cl(const KArgs &a, int cluster, int n_clusters, cudaStream_t st) {
     if (cluster < 1 || cluster > kMaxG || n_clusters < 1) return cudaErrorInvalidValue;
     const bool put = (a.jobs ? a.jobs_type : a.one.type) == AMC_PUT;
-    const void *f = put ? (const void *)sweep_cl_kernel<true> : (const void *)sweep_cl_kernel<false>;
-    const size_t smem = sizeof(SmemCl);
+    void (*kern)(KArgs) = a.h16 ? (put ? sweep_cl_kernel<true, true> : sweep_cl_kernel<false, true>)
+                                : (put ? sweep_cl_kernel<true, false> : sweep_cl_kernel<false, false>);
+    const void *f = (const void *)kern;
+    const size_t smem = a.h16 ? sizeof(SmemCl<uint16_t>) : sizeof(SmemCl<float>);
     cudaError_t e = ensure_smem(f, smem);
     if (e != cudaSuccess) return e;
     if (cluster > 8) {
@@ -688,23 +695,25 @@ cudaError_t launch_sweep_cl(const KArgs &a, int cluster, int n_clusters, cudaStr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, put ? sweep_cl_kernel<true> : sweep_cl_kernel<false>, a);
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // Largest cluster of this kernel that the current device can hold at once
 // (0 if none): a 16-CTA cluster needs 16 SMs of one GPC with room for a
-// 1024-thread CTA and its ring.
+// 1024-thread CTA and its ring.  Taken with the FP32 ring; the binary16
+// ring is smaller, so the binary16 variants hold at least as many.
 cudaError_t sweep_cl_max_cluster(int *out) {
     *out = 0;
-    const void *f = (const void *)sweep_cl_kernel<true>;
-    const size_t smem = sizeof(SmemCl);
+    const void *f = (const void *)sweep_cl_kernel<true, false>;
+    const size_t smem = sizeof(SmemCl<float>);
     cudaError_t e = ensure_smem(f, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)sweep_cl_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute((const void *)sweep_cl_kernel<false, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1);
     if (e != cudaSuccess) return e;
-    e = ensure_smem((const void *)sweep_cl_kernel<false>, smem);
+    e = ensure_smem((const void *)sweep_cl_kernel<false, false>, smem);
     if (e != cudaSuccess) return e;
     for (int g = kMaxG; g >= 1; --g) {
         cudaLaunchConfig_t cfg = {};

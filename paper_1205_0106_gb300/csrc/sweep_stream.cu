@@ -26,7 +26,7 @@
 //     per-CTA FP64 sums of CF and CF^2 for finalize_kernel, which applies the
 //     last e^{-r dt}.
 // Traffic per path and date: S_j and S_{j+1} read, CF read and written
-// (16 bytes in FP32).  Deterministic: fixed grid, fixed path ranges, fixed
+// (16 bytes in FP32; 12 when the path array holds binary16 moneyness).  Deterministic: fixed grid, fixed path ranges, fixed
 // reduction order.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -64,6 +64,33 @@ __device__ __forceinline__ void ld4(const double *p, double *o) {
     const double2 b = reinterpret_cast<const double2 *>(p)[1];
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
+// y = S/K - 1 of 4 consecutive paths from a row of the path array: FP32 or
+// FP64 prices, or binary16 moneyness (AMC_MIXED16), widened exactly.
+__device__ __forceinline__ void ldy4(const float *p, float invK, float *y) {
+    ld4(p, y);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) y[e] = fmaf(y[e], invK, -1.f);
+}
+__device__ __forceinline__ void ldy4(const double *p, double invK, double *y) {
+    ld4(p, y);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) y[e] = fma(y[e], invK, -1.0);
+}
+__device__ __forceinline__ void ldy4(const uint16_t *p, float, float *y) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    const dev::f2 a = dev::h2_to_f2(w.x), b = dev::h2_to_f2(w.y);
+    y[0] = dev::f2_lo(a); y[1] = dev::f2_hi(a); y[2] = dev::f2_lo(b); y[3] = dev::f2_hi(b);
+}
+// Programmatic dependent launch: the passes and solves are launched so that
+// the next kernel of the stream may start once every CTA of the current
+// one has signalled (at its start), and each waits in griddepcontrol.wait,
+// until the previous kernel has completed and its writes are visible,
+// before it reads what that kernel wrote.  The wait is the hardware's own:
+// it ends when the previous grid ends.  Launched without the attribute
+// both instructions do nothing.
+__device__ __forceinline__ void pdl_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void st4(float *p, const float *v) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -196,31 +223,53 @@ struct PathSums<false> {
     }
 };
 
-// Per-CTA totals of the kNV accumulators, in thread 0.  FP32 path: double-
-// float through the warp tree and the CTA (the FP64 pipe of this GPU is
-// slow; a tree of doubles here costs more than the pass's memory traffic);
-// FP64 path: doubles.  Fixed order in both.
+// Per-CTA totals of the kNV accumulators.  FP32 path: double-float through
+// the warp and the CTA (the FP64 pipe of this GPU is slow; a tree of
+// doubles here costs more than the pass's memory traffic), thread k ending
+// with total k; FP64 path: doubles, all totals in thread 0.  Fixed order in
+// both.
 struct DfRed {
     dev::dfl w[kStreamThreads / 32][kNV];
 };
 struct DRed {
     double w[kStreamThreads / 32][kNV];
 };
-__device__ __forceinline__ void cta_totals(Acc<false> (&acc)[kNV], DfRed &red, dev::dfl (&tot)[kNV]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+// Fixed-order warp sums of 16 double-float values by a transposed
+// butterfly: at offsets 16, 8, 4 and 2 each lane keeps half of its values
+// (the upper half where the offset bit of its index is set) and adds the
+// partner's copy of that half, so a lane exchanges 8 + 4 + 2 + 1 values
+// instead of 5 per value; offset 1 is an ordinary butterfly step.  Lane l
+// ends with the warp's sum of value (l >> 1) & 15.
+__device__ __forceinline__ dev::dfl df_warp_sum16(dev::dfl (&v)[16], int lane) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) {
-        const dev::dfl d = dev::df_warp_sum(acc[k].get_df());
-        if (lane == 0) red.w[warp][k] = d;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
+    for (int h = 8; h >= 1; h >>= 1) {
+        const int off = 2 * h;
+        const bool up = (lane & off) != 0;
 #pragma unroll
-        for (int k = 0; k < kNV; ++k) {
-            dev::dfl t = red.w[0][k];
-            for (int w = 1; w < kStreamThreads / 32; ++w) t = dev::df_add(t, red.w[w][k]);
-            tot[k] = t;
+        for (int i = 0; i < h; ++i) {
+            const dev::dfl send = up ? v[i] : v[i + h];
+            const dev::dfl keep = up ? v[i + h] : v[i];
+            v[i] = dev::df_add(keep, dev::df_shfl_xor(send, off));
         }
+    }
+    return dev::df_add(v[0], dev::df_shfl_xor(v[0], 1));
+}
+
+// CTA total of value k (k < kNV) in thread k from one double-float per
+// value and thread: the warp sums above, then the warps' sums in warp order.
+__device__ __forceinline__ dev::dfl cta_total_df(dev::dfl (&v)[16], DfRed &red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const dev::dfl s = df_warp_sum16(v, lane);
+    const int k = lane >> 1;
+    if ((lane & 1) == 0 && k < kNV) red.w[warp][k] = s;
+    __syncthreads();
+    dev::dfl t = {0.f, 0.f};
+    if (threadIdx.x < kNV) {
+        t = red.w[0][threadIdx.x];
+        for (int w = 1; w < kStreamThreads / 32; ++w) t = dev::df_add(t, red.w[w][threadIdx.x]);
+    }
+    return t;
 }
 __device__ __forceinline__ void cta_totals(Acc<true> (&acc)[kNV], DRed &red, double (&tot)[kNV]) {
     double v[kNV];
@@ -235,17 +284,22 @@ __device__ __forceinline__ double to_d(double x) { return x; }
 
 
 // One exercise date: j = 1 .. m-1 sums the moments of date j; j = 0 is the
-// final pass (exercise of date 1, sums of CF).
-template <bool FP64, bool PUT>
+// final pass (exercise of date 1, sums of CF).  H16: the path array holds
+// binary16 moneyness (12 instead of 16 bytes per path and date).
+template <bool FP64, bool PUT, bool H16>
 __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_constant__ StreamArgs a, int j) {
+    static_assert(!(FP64 && H16), "binary16 moneyness is an FP32-path format");
     using Real = typename ST<FP64>::Real;
+    using Elem = typename std::conditional<H16, uint16_t, Real>::type;
     using Red = typename std::conditional<FP64, DRed, DfRed>::type;
     using Tot = typename std::conditional<FP64, double, dev::dfl>::type;
     __shared__ Red red;
+    pdl_signal();
+    pdl_wait();                                             // the cash flows, beta and flags of the last kernels
     const Job &J = a.one;
     const int m = J.m, p = J.p;
     const int64_t N = J.N, ld = J.ld;
-    const Real *__restrict__ S = reinterpret_cast<const Real *>(J.S);
+    const Elem *__restrict__ S = reinterpret_cast<const Elem *>(J.S);
     Real *__restrict__ cf = reinterpret_cast<Real *>(a.cf);
     const Real invK = (Real)J.invK, disc = (Real)J.disc;
     // exercise boundary of date j+1 (row j), unless the pass starts at maturity
@@ -265,23 +319,23 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_c
     for (int64_t g = (int64_t)blockIdx.x * kStreamThreads + threadIdx.x; g < groups;
          g += (int64_t)gridDim.x * kStreamThreads) {
         const int64_t i0 = 4 * g;
-        Real v[4], s[4], sj[4];
-        if (j >= 1) ld4(S + (int64_t)(j - 1) * ld + i0, sj);     // S_j, issued with the other rows
+        Real v[4], ye[4], yj[4];
+        if (j >= 1) ldy4(S + (int64_t)(j - 1) * ld + i0, invK, yj);   // date j, issued with the other rows
         if (init) {
-            ld4(S + (int64_t)(m - 1) * ld + i0, s);         // S_m
+            ldy4(S + (int64_t)(m - 1) * ld + i0, invK, ye);          // maturity
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const Real y = fma(s[e], invK, Real(-1));
+                const Real y = ye[e];
                 const Real h = PUT ? -y : y;
                 v[e] = h > Real(0) ? h : Real(0);
             }
         } else {
             ld4(cf + i0, v);
             if (exer) {
-                ld4(S + (int64_t)(ed - 1) * ld + i0, s);    // S_{j+1}
+                ldy4(S + (int64_t)(ed - 1) * ld + i0, invK, ye);   // date j+1
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const Real y = fma(s[e], invK, Real(-1));
+                    const Real y = ye[e];
                     const Real h = PUT ? -y : y;
                     const Real cont = fma(fma(fma(c3, y, c2), y, c1), y, c0);
                     if ((PUT ? y < Real(0) : y > Real(0)) && h > cont) v[e] = h;
@@ -295,7 +349,7 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_c
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (i0 + e >= N) continue;
-                const Real y = fma(sj[e], invK, Real(-1));
+                const Real y = yj[e];
                 if (!(PUT ? y < Real(0) : y > Real(0))) continue;      // in the money, strictly
                 sums.add_path(y, v[e], p);
             }
@@ -310,33 +364,51 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_c
     }
     Acc<FP64> acc[kNV];
     sums.get(acc);
-    Tot tot[kNV];
-    cta_totals(acc, red, tot);
-    if (threadIdx.x == 0) {
-        if (j >= 1) {
-            Tot *row = reinterpret_cast<Tot *>(a.part) + (int64_t)blockIdx.x * kNV;
+    Tot *row = reinterpret_cast<Tot *>(a.part) + (int64_t)blockIdx.x * kNV;
+    double *fin = reinterpret_cast<double *>(J.fin) + (int64_t)blockIdx.x * 4;
+    if constexpr (FP64) {
+        Tot tot[kNV];
+        cta_totals(acc, red, tot);
+        if (threadIdx.x == 0) {
+            if (j >= 1) {
 #pragma unroll
-            for (int k = 0; k < kNV; ++k) row[k] = tot[k];
-        } else {
-            double *fin = reinterpret_cast<double *>(J.fin) + (int64_t)blockIdx.x * 4;
-            fin[0] = J.K * to_d(tot[0]);
-            fin[1] = J.K * J.K * to_d(tot[1]);
-            fin[2] = 0.0;
-            fin[3] = 0.0;
-            if (blockIdx.x == 0) J.res[4] = (double)*a.ndeg;
+                for (int k = 0; k < kNV; ++k) row[k] = tot[k];
+            } else {
+                fin[0] = J.K * to_d(tot[0]);
+                fin[1] = J.K * J.K * to_d(tot[1]);
+                fin[2] = 0.0;
+                fin[3] = 0.0;
+                if (blockIdx.x == 0) J.res[4] = (double)*a.ndeg;
+            }
+        }
+    } else {
+        dev::dfl v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = k < kNV ? acc[k].get_df() : dev::dfl{0.f, 0.f};
+        const dev::dfl t = cta_total_df(v, red);
+        const int k = threadIdx.x;
+        if (j >= 1) {
+            if (k < kNV) row[k] = t;
+        } else if (k < 4) {
+            fin[k] = k == 0 ? J.K * to_d(t) : (k == 1 ? J.K * J.K * to_d(t) : 0.0);
+            if (blockIdx.x == 0 && k == 0) J.res[4] = (double)*a.ndeg;
         }
     }
 }
 
-// Solve of date j from the partial rows: fixed-order FP64 sums (thread t
-// adds rows t, t + kStreamThreads, ..), a fixed tree, then one thread.
+// Solve of date j from the partial rows: fixed-order sums (thread t adds
+// rows t, t + kStreamThreads, ..; double-float, or FP64 under AMC_FP64), a
+// fixed tree, then warp 0.
 template <bool FP64>
 __global__ void __launch_bounds__(kStreamThreads) lsm_stream_solve(const __grid_constant__ StreamArgs a, int j) {
+    pdl_signal();
+    pdl_wait();                                             // the pass's partial rows
     const Job &J = a.one;
     const int p = J.p;
-    double tot[kNV];
+    __shared__ double sM[kNV], sA[16], sP[4];
     if constexpr (FP64) {
         __shared__ double red[kStreamThreads / 32][kNV];
+        double tot[kNV];
 #pragma unroll
         for (int k = 0; k < kNV; ++k) tot[k] = 0.0;
         for (int c = threadIdx.x; c < a.grid; c += kStreamThreads) {
@@ -345,39 +417,26 @@ __global__ void __launch_bounds__(kStreamThreads) lsm_stream_solve(const __grid_
             for (int k = 0; k < kNV; ++k) tot[k] += row[k];
         }
         block_sum_d<kNV>(tot, red);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < kNV; ++k) sM[k] = tot[k];
     } else {
         __shared__ DfRed red;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        dev::dfl t[kNV];
+        dev::dfl t[16];
 #pragma unroll
-        for (int k = 0; k < kNV; ++k) t[k] = {0.f, 0.f};
+        for (int k = 0; k < 16; ++k) t[k] = {0.f, 0.f};
         for (int c = threadIdx.x; c < a.grid; c += kStreamThreads) {
             const dev::dfl *row = reinterpret_cast<const dev::dfl *>(a.part) + (int64_t)c * kNV;
 #pragma unroll
             for (int k = 0; k < kNV; ++k) t[k] = dev::df_add(t[k], row[k]);
         }
-#pragma unroll
-        for (int k = 0; k < kNV; ++k) {
-            const dev::dfl d = dev::df_warp_sum(t[k]);
-            if (lane == 0) red.w[warp][k] = d;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0)
-#pragma unroll
-            for (int k = 0; k < kNV; ++k) {
-                dev::dfl u = red.w[0][k];
-                for (int w = 1; w < kStreamThreads / 32; ++w) u = dev::df_add(u, red.w[w][k]);
-                tot[k] = to_d(u);
-            }
+        const dev::dfl u = cta_total_df(t, red);
+        if (threadIdx.x < kNV) sM[threadIdx.x] = to_d(u);
     }
+    __syncthreads();
     // the inverse of the Gram matrix by cofactors over warp 0 (FP64 chains a
     // few operations deep: this GPU's FP64 latency makes a one-thread
     // Cholesky the longest step of a date), then beta_k = sum_l Ginv_kl R_l
-    __shared__ double sM[kNV], sA[16], sP[4];
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < kNV; ++k) sM[k] = tot[k];
-    __syncthreads();
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     bool degen = false;
@@ -420,34 +479,48 @@ __global__ void lsm_stream_coef_m1(const __grid_constant__ StreamArgs a) {
 
 namespace {
 using PassFn = void (*)(StreamArgs, int);
-PassFn pass_fn(bool fp64, bool put) {
-    return fp64 ? (put ? lsm_stream_pass<true, true> : lsm_stream_pass<true, false>)
-                : (put ? lsm_stream_pass<false, true> : lsm_stream_pass<false, false>);
+PassFn pass_fn(bool fp64, bool put, bool h16) {
+    if (h16) return put ? lsm_stream_pass<false, true, true> : lsm_stream_pass<false, false, true>;
+    return fp64 ? (put ? lsm_stream_pass<true, true, false> : lsm_stream_pass<true, false, false>)
+                : (put ? lsm_stream_pass<false, true, false> : lsm_stream_pass<false, false, false>);
 }
 }  // namespace
 
 // As many CTAs as fit on the SMs at once.
-int64_t stream_grid(int sm_count, bool fp64, bool put) {
+int64_t stream_grid(int sm_count, bool fp64, bool put, bool h16) {
     int per = 0;
-    if (ctas_per_sm((const void *)pass_fn(fp64, put), kStreamThreads, 0, &per) != cudaSuccess || per < 1) per = 1;
+    if (ctas_per_sm((const void *)pass_fn(fp64 && !h16, put, h16), kStreamThreads, 0, &per) != cudaSuccess || per < 1)
+        per = 1;
     return (int64_t)per * sm_count;
 }
 
 cudaError_t launch_lsm_stream(const StreamArgs &a, bool fp64, cudaStream_t st) {
     const Job &J = a.one;
-    const PassFn pass = pass_fn(fp64, J.type == AMC_PUT);
-    const unsigned g = (unsigned)a.grid;
+    if (fp64 && a.h16) return cudaErrorInvalidValue;
+    const PassFn pass = pass_fn(fp64, J.type == AMC_PUT, a.h16 != 0);
+    void (*solve)(StreamArgs, int) = fp64 ? lsm_stream_solve<true> : lsm_stream_solve<false>;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cp = {}, cs = {};
+    cp.gridDim = dim3((unsigned)a.grid);
+    cp.blockDim = dim3(kStreamThreads);
+    cp.stream = st;
+    cp.attrs = attr;
+    cp.numAttrs = 1;
+    cs = cp;
+    cs.gridDim = dim3(1);
+    cudaError_t e = cudaSuccess;
     if (J.m == 1) {
         lsm_stream_coef_m1<<<1, 32, 0, st>>>(a);
     } else {
-        for (int j = J.m - 1; j >= 1; --j) {
-            pass<<<g, kStreamThreads, 0, st>>>(a, j);
-            if (fp64) lsm_stream_solve<true><<<1, kStreamThreads, 0, st>>>(a, j);
-            else lsm_stream_solve<false><<<1, kStreamThreads, 0, st>>>(a, j);
+        for (int j = J.m - 1; j >= 1 && e == cudaSuccess; --j) {
+            e = cudaLaunchKernelEx(&cp, pass, a, j);
+            if (e == cudaSuccess) e = cudaLaunchKernelEx(&cs, solve, a, j);
         }
     }
-    pass<<<g, kStreamThreads, 0, st>>>(a, 0);
-    return cudaGetLastError();
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cp, pass, a, 0);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace amc

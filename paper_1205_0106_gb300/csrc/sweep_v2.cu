@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "devutil.cuh"
 #include "internal.h"
 #include "lsm_solve.cuh"
@@ -53,8 +55,10 @@ constexpr int kSolvers = 2;                 // solver warps 0 and 1 take alterna
 constexpr int kW0 = 32 * kSolvers;          // first path thread
 constexpr int kXW0 = kSolvers;              // exchange warps kXW0 .. kXW0+10
 
+// E: float (FP32 prices) or uint16_t (binary16 moneyness, AMC_MIXED16)
+template <typename E>
 struct SmemV2 {
-    float S[kSlots][kPPC];
+    E S[kSlots][kPPC];
     uint64_t mbar[kSlots];
     float redG[2][32][7];           // warp sums of Gram moments (Gram warps), by exchange parity
     float redR[32][4];              // warp sums of right-hand sides (path warps)
@@ -179,21 +183,23 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
 }
 
-template <bool GREEKS, bool PUT>
+template <bool GREEKS, bool PUT, bool H16>
 __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_constant__ KArgs a) {
+    static_assert(!(GREEKS && H16), "the Greeks variant needs the prices: FP32 paths only");
+    using E = typename std::conditional<H16, uint16_t, float>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemV2 &sm = *reinterpret_cast<SmemV2 *>(smem_raw);
+    SmemV2<E> &sm = *reinterpret_cast<SmemV2<E> *>(smem_raw);
     const int jb = a.jobs ? find_job_by_cta(a.jobs, a.n_jobs, blockIdx.x) : 0;
     const Job &J = a.jobs ? a.jobs[jb] : a.one;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lc = blockIdx.x - J.cta_begin, G = J.n_cta;
     const int m = J.m, p = J.p, nmom = 2 * p - 1;
     const float invK = (float)J.invK, disc = (float)J.disc;
-    const float *__restrict__ S = reinterpret_cast<const float *>(J.S);
+    const E *__restrict__ S = reinterpret_cast<const E *>(J.S);
     const int64_t N = J.N, ld = J.ld;
     const int64_t base = (int64_t)lc * kPPC;
     const int64_t rem = ld - base;
-    const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * 4u;
+    const uint32_t slice_bytes = (uint32_t)(rem < kPPC ? rem : kPPC) * (uint32_t)sizeof(E);
     const int nloc = (N - base) < kPPC ? (int)(N - base) : kPPC;      // own paths below N
     uint64_t *const xch = J.xch;
     int32_t *const status = J.status;
@@ -261,10 +267,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
 
     // ------------------------------------------------------------ path warps
     // Per-path state is held in units of K: cash flow cf, and for Greeks the
-    // stopping date and y = S/K - 1 at stopping.  The ring slots hold S as
-    // copied from HBM until the Gram pass of that date rewrites them in place
-    // as y for in-the-money own paths and 0 otherwise; later passes then need
-    // no payoff, moneyness or validity arithmetic (ITM <=> y != 0).
+    // stopping date and y = S/K - 1 at stopping.  The ring slots hold S (or
+    // the binary16 y) as copied from HBM until the Gram pass of that date
+    // rewrites them in place as y for in-the-money own paths and 0 otherwise;
+    // later passes then need no payoff, moneyness or validity arithmetic
+    // (ITM <=> y != 0).
     // Per date all 30 path warps run the exercise and right-hand-side pass
     // and, after the post, the Gram pass of a later date over their own 8
     // paths; warps kXW0..kXW0+10 also post and gather one exchanged value
@@ -306,10 +313,9 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         float g[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) g[k] = 0.f;
-        float *sl = sm.S[d % kSlots];
+        E *sl = sm.S[d % kSlots];
         const float big = PUT ? -0x1p100f : 0x1p100f;
-        auto one = [&](float s, bool valid, float &yo) {
-            const float yr = fmaf(s, invK, -1.f);
+        auto one = [&](float yr, bool valid, float &yo) {
             const float in = valid ? __saturatef(yr * big) : 0.f;
             const float y = valid ? yr * in : 0.f;
             yo = y;
@@ -325,11 +331,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
 #pragma unroll
         for (int i = 0; i < kPPT; i += 2) {
             const int idx = pidx(i);
-            const float2 s2 = *reinterpret_cast<const float2 *>(sl + idx);
-            float2 y2;
-            one(s2.x, idx < nloc, y2.x);
-            one(s2.y, idx + 1 < nloc, y2.y);
-            *reinterpret_cast<float2 *>(sl + idx) = y2;
+            const f2 yr = raw_y2(sl, idx, invK);
+            float ylo, yhi;
+            one(f2_lo(yr), idx < nloc, ylo);
+            one(f2_hi(yr), idx + 1 < nloc, yhi);
+            put_y2(sl, idx, f2_pack(ylo, yhi));
         }
         fence_proxy_async();             // these generic writes precede a later TMA refill
         const float r = warp_sum8(g, lane);
@@ -348,11 +354,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     int degenerate = 0;
     const bool ok = wait_slice(m);
     if (ok) {
-        const float *sl = sm.S[m % kSlots];
+        const E *sl = sm.S[m % kSlots];
 #pragma unroll
         for (int i = 0; i < kPPT; ++i) {
             const int idx = pidx(i);
-            const float y = fmaf(sl[idx], invK, -1.f);
+            const float y = raw_y(sl, idx, invK);
             const float h = PUT ? -y : y;
             cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
             if (GREEKS) {
@@ -370,11 +376,11 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     // (packed f32x2 pairs; the Greeks variant, which also carries the
     // stopping date and moneyness per path, stays scalar for its registers)
     auto exercise = [&](int d, float b0, float b1, float b2, float b3) {
-        const float *sl = sm.S[d % kSlots];
+        const E *sl = sm.S[d % kSlots];
         if (GREEKS) {
 #pragma unroll
             for (int i = 0; i < kPPT; ++i) {
-                const float y = sl[pidx(i)];
+                const float y = y_at(sl, pidx(i));
                 const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
                 const float h = PUT ? -y : y;
                 const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
 #pragma unroll
         for (int i = 0; i < kPPT; i += 2) {
-            const f2 Y = *reinterpret_cast<const f2 *>(sl + pidx(i));
+            const f2 Y = y2_at(sl, pidx(i));
             const f2 C = f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0);
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
@@ -421,12 +427,12 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 }
             }
             float rr[4] = {0.f, 0.f, 0.f, 0.f};
-            const float *sl = sm.S[j % kSlots];
+            const E *sl = sm.S[j % kSlots];
             if (GREEKS) {
 #pragma unroll
                 for (int i = 0; i < kPPT; ++i) {
                     cf[i] *= disc;
-                    const float y = sl[pidx(i)];
+                    const float y = y_at(sl, pidx(i));
                     const float c = y != 0.f ? cf[i] : 0.f;
                     const float yy = y * y;
                     rr[0] += c;
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                 f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
 #pragma unroll
                 for (int i = 0; i < kPPT; i += 2) {
-                    const f2 Y = *reinterpret_cast<const f2 *>(sl + pidx(i));
+                    const f2 Y = y2_at(sl, pidx(i));
                     const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
                     cf[i] = f2_lo(C);
                     cf[i + 1] = f2_hi(C);
@@ -645,9 +651,15 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
 
 cudaError_t launch_sweep_lsm_v2(const KArgs &a, int total_ctas, bool greeks, cudaStream_t st) {
     const bool put = (a.jobs ? a.jobs_type : a.one.type) == AMC_PUT;
-    const void *f = greeks ? (put ? (const void *)sweep_lsm_v2_kernel<true, true> : (const void *)sweep_lsm_v2_kernel<true, false>)
-                           : (put ? (const void *)sweep_lsm_v2_kernel<false, true> : (const void *)sweep_lsm_v2_kernel<false, false>);
-    const int smem = (int)sizeof(SmemV2);
+    if (greeks && a.h16) return cudaErrorInvalidValue;
+    const void *f;
+    if (a.h16)
+        f = put ? (const void *)sweep_lsm_v2_kernel<false, true, true> : (const void *)sweep_lsm_v2_kernel<false, false, true>;
+    else if (greeks)
+        f = put ? (const void *)sweep_lsm_v2_kernel<true, true, false> : (const void *)sweep_lsm_v2_kernel<true, false, false>;
+    else
+        f = put ? (const void *)sweep_lsm_v2_kernel<false, true, false> : (const void *)sweep_lsm_v2_kernel<false, false, false>;
+    const int smem = (int)(a.h16 ? sizeof(SmemV2<uint16_t>) : sizeof(SmemV2<float>));
     cudaError_t e = ensure_smem(f, (size_t)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};

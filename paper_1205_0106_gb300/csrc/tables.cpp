@@ -200,14 +200,15 @@ int64_t host_ld(int64_t n_paths) { return (n_paths + 31) / 32 * 32; }
 // option's reduction order is the same alone or batched.
 int host_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, SweepPlan *p, int max_cluster) {
     if (n_paths < 1 || sm_count < 1) return AMC_EINVAL;
-    if (prec == AMC_MIXED && rule == AMC_RULE_LSM && max_cluster >= 1 &&
+    const bool mixed_lsm = (prec == AMC_MIXED || prec == AMC_MIXED16) && rule == AMC_RULE_LSM;
+    if (mixed_lsm && max_cluster >= 1 &&
         n_paths <= (int64_t)std::min(max_cluster, kClMaxCluster) * kClPathsPerCta) {
         p->kind = 3;                                  // one cluster per option
         p->chunks = kClPPT;
         p->ctas = (int)((n_paths + kClPathsPerCta - 1) / kClPathsPerCta);
         return AMC_OK;
     }
-    if (prec == AMC_MIXED && rule == AMC_RULE_LSM) {
+    if (mixed_lsm) {
         const int64_t g = (n_paths + kV2PathsPerCta - 1) / kV2PathsPerCta;
         if (g > sm_count || g > kV2MaxCtas) return AMC_EINVAL;   // per-path state must stay on chip
         p->kind = 2;

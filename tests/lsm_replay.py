@@ -66,28 +66,35 @@ import oracle
 U = 2.0 ** -24
 
 
-def gpu_fit(amc, ctx, torch, o, streaming=False):
+def gpu_fit(amc, ctx, torch, o, streaming=False, h16=False):
     """The GPU's FP32 paths of option o (exact values as float64 [m, N]), the
     boundary its mixed sweep fits on them ([m, AMC_COEF_STRIDE]) and its
     in-sample result dict; streaming: the streaming sweep of large options
-    (forced by amc_ctx_inject kind 3) instead of the register-resident one."""
+    (forced by amc_ctx_inject kind 3) instead of the register-resident one;
+    h16: the binary16 moneyness path array (AMC_MIXED16), returned as the
+    prices K (1 + y) in FP64 (the sweep reads y exactly, so the bound on dy
+    below holds with room to spare)."""
     ld = amc.amc_path_ld(o.n_paths)
-    S = torch.empty((o.n_steps, ld), dtype=torch.float32, device="cuda")
+    prec = amc.AMC_MIXED16 if h16 else amc.AMC_MIXED
+    S = torch.empty((o.n_steps, ld), dtype=torch.float16 if h16 else torch.float32, device="cuda")
     coef = torch.full((o.n_steps, amc.AMC_COEF_STRIDE), float("nan"), dtype=torch.float64, device="cuda")
     res = torch.zeros(amc.AMC_RES_DOUBLES, dtype=torch.float64, device="cuda")
-    amc.amc_generate_paths(ctx, o, amc.AMC_MIXED, S)
+    amc.amc_generate_paths(ctx, o, prec, S)
     if streaming:
         ctx.inject(3)
-    amc.amc_fit_boundary(ctx, o, amc.AMC_MIXED, S, coef, res)
+    amc.amc_fit_boundary(ctx, o, prec, S, coef, res)
     torch.cuda.synchronize()
-    return (S[:, :o.n_paths].double().cpu().numpy(), coef.cpu().numpy(), amc.res_to_dict(res.cpu().numpy()))
+    Sh = S[:, :o.n_paths].double().cpu().numpy()
+    if h16:
+        Sh = o.K * (1.0 + Sh)
+    return Sh, coef.cpu().numpy(), amc.res_to_dict(res.cpu().numpy())
 
 
-def gpu_replay(amc, ctx, o, streaming=False):
+def gpu_replay(amc, ctx, o, streaming=False, h16=False):
     """gpu_fit then replay_check: the mixed sweep of o held to its FP32
     arithmetic on its own paths."""
     import torch
-    S, coef, res = gpu_fit(amc, ctx, torch, o, streaming=streaming)
+    S, coef, res = gpu_fit(amc, ctx, torch, o, streaming=streaming, h16=h16)
     return replay_check(S, o, coef, res)
 
 

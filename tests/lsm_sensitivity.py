@@ -83,3 +83,32 @@ def check_mixed_vs_oracle(o, got, ref, fp64_price, replay, bar=2e-4):
     assert spread > bar / 2, ("mixed price off the oracle on an FP32-stable option", o, got, ref, spread)
     replay()
     assert abs(fp64_price() - ref) <= bar * o.K, (o, ref)
+
+
+def binary16_moneyness(S, K):
+    """Paths S (FP64) with their moneyness y = S/K - 1 rounded to IEEE
+    binary16 (round to nearest even), as prices K (1 + y)."""
+    return K * (1.0 + (S / K - 1.0).astype(np.float16).astype(np.float64))
+
+
+def binary16_shift(o):
+    """|oracle price on the binary16-rounded paths - oracle price| / K."""
+    S = paths(o)
+    ref = oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"]
+    return abs(oracle.lsm(binary16_moneyness(S, o.K), o.type, o.K, o.r, o.T, o.basis)["price"] - ref) / o.K
+
+
+def check_mixed16_vs_oracle(o, got, ref, fp64_price, replay, bar=2e-4):
+    """As check_mixed_vs_oracle for the binary16 path array (AMC_MIXED16):
+    a price off the oracle by more than bar K is accepted only on an option
+    whose oracle price itself moves by more than half the bar when its paths
+    are rounded to binary16 moneyness (or under FP32-level noise); the
+    kernel is then held to the replay check on its own binary16 paths and
+    the FP64 GPU price to bar K."""
+    err = abs(got - ref) / o.K
+    if err <= bar:
+        return
+    spread = max(binary16_shift(o), path_noise_spread(o, reps=2))
+    assert spread > bar / 2, ("binary16 price off the oracle on a stable option", o, got, ref, spread)
+    replay()
+    assert abs(fp64_price() - ref) <= bar * o.K, (o, ref)

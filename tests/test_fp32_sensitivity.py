@@ -46,15 +46,19 @@ def test_deep_in_the_money_call_of_the_batch_is_unstable_at_fp32_precision():
 
 
 def test_sixteen_bit_log_moneyness_storage_error():
-    """Error study for storing the path array as log(S/K) in 16 bits: on the
+    """Error study for storing the path array in 16 bits: on the
     Longstaff-Schwartz Table 1 put and the 252-date put (2^16 paths), the
-    oracle's price on the rounded paths moves by less than 1e-4 K in FP16
-    and in BF16 (round to nearest even), half the price bar."""
+    oracle's price on the rounded paths moves by less than 1e-4 K, half the
+    price bar, with log(S/K) in FP16 or in BF16 (round to nearest even) and
+    with the moneyness y = S/K - 1 in FP16 (the AMC_MIXED16 format)."""
     import numpy as np
 
     import oracle
+    from lsm_sensitivity import binary16_moneyness
 
     def rounded(S, K, kind):
+        if kind == "y16":
+            return binary16_moneyness(S, K)
         x = np.log(S / K)
         if kind == "fp16":
             xq = x.astype(np.float16).astype(np.float64)
@@ -67,6 +71,17 @@ def test_sixteen_bit_log_moneyness_storage_error():
     for o in (STABLE, workloads.scaled(workloads.single_large(), n_paths=2 ** 16)):
         S = oracle.paths(o.S0, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.seed)
         ref = oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"]
-        for kind in ("fp16", "bf16"):
+        for kind in ("fp16", "bf16", "y16"):
             got = oracle.lsm(rounded(S, o.K, kind), o.type, o.K, o.r, o.T, o.basis)["price"]
             assert abs(got - ref) < 1e-4 * o.K, (o, kind, got, ref)
+
+
+def test_binary16_moneyness_rounding_moves_an_unstable_batch_option_beyond_the_bar():
+    """Batch option 2, a call with S0/K = 1.26, sigma 41 % and basis 3 (the
+    unstable kind above): rounding its paths to binary16 moneyness moves the
+    oracle's own price by more than 2e-4 K, so AMC_MIXED16 cannot meet the
+    price bar there and the GPU tests hold it to the replay check instead."""
+    from lsm_sensitivity import binary16_shift
+    o = workloads.scaled(workloads.batch_options()[2], n_paths=2 ** 14)
+    assert o.type == 1 and o.basis == 3
+    assert binary16_shift(o) > 2e-4
