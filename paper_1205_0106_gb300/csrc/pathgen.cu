@@ -50,6 +50,24 @@ struct PG<true> {
     using Node = NodeD;
 };
 
+template <typename Real>
+struct alignas(4 * sizeof(Real)) R4 {
+    Real v[4];
+};
+
+// A bridge node as pathgen_kernel reads it, expanded from NodeF/NodeD once
+// per job: shared-memory offsets instead of indices, and the job's scale
+// factors applied (the same products the node loop would form).
+template <typename Real>
+struct alignas(16) NodeX {
+    int32_t v4;                   // first of the dimension's 3 uint4 of direction numbers
+    int32_t coord;                // Sobol' dimension
+    int32_t wl_o, wr_o, wo_o;     // byte offsets of the left, right and own stack slots
+    int32_t date;
+    Real wl, wr, sd, drift;       // bridge weights, sdu sqrt(dt), mu dt date (base 2 in FP32)
+    int64_t row;                  // (date - 1) ld: element offset of the date's row
+};
+
 // Shared-memory layout of the path-generation kernel: every sub-buffer
 // starts on a 32-byte boundary (uint4 and R4<double> accesses).  A kernel
 // that values a fitted boundary on the fly also holds the boundary (four
@@ -63,7 +81,8 @@ __host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int ns
     const bool boundary = mode == 3;
     const unsigned per_date = boundary ? 4u : (mode == 1 ? 2u : 0u);
     PathgenSmem L;
-    const unsigned node = fp64 ? (unsigned)sizeof(NodeD) : (unsigned)sizeof(NodeF);
+    const unsigned node = fp64 ? (unsigned)sizeof(NodeX<double>) : (unsigned)sizeof(NodeX<float>);
+    static_assert(sizeof(NodeX<double>) >= sizeof(NodeD) && sizeof(NodeX<float>) >= sizeof(NodeF), "node region");
     const unsigned real = fp64 ? 8u : 4u;
     L.nodes = 0;
     L.v = al32(L.nodes + node * (unsigned)max_m);
@@ -84,15 +103,12 @@ __device__ __forceinline__ int find_job_by_tile(const Job *__restrict__ jobs, in
     return lo;
 }
 
-template <typename Real>
-struct alignas(4 * sizeof(Real)) R4 {
-    Real v[4];
-};
-
 // The 4 points of one bridge node: z = N^{-1}(u) of the Sobol' integers xq,
 // W = wl W_left + wr W_right + sd z (ref. [13]), S = S0 exp(drift + sig W)
 // + off (Eq. 9 in log space; base 2 in FP32).  off = 0 gives S; S0 / K for
-// S0 and off = -1 give the moneyness y = S/K - 1 with one rounding.
+// S0 and off = -1 give the moneyness y = S/K - 1 with one rounding.  In
+// FP32 xq holds the integers with the top bit flipped, so that as signed
+// values they are x - 2^31 (the uniform's offset from 1/2).
 template <bool FP64, typename Real>
 __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Real wr, Real sd, Real drift,
                                             Real sig, Real S0, Real off, const R4<Real> &Wl, const R4<Real> &Wr,
@@ -115,8 +131,7 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
         bool tail = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const f2 y = f2_fma(f2_pack((float)(int32_t)(xq[2 * h] ^ 0x80000000u),
-                                        (float)(int32_t)(xq[2 * h + 1] ^ 0x80000000u)),
+            const f2 y = f2_fma(f2_pack((float)(int32_t)xq[2 * h], (float)(int32_t)xq[2 * h + 1]),
                                 f2_splat(0x1p-32f), f2_splat(0x1p-33f));
             const f2 zc = icdf_central2(y);
             yv[2 * h] = f2_lo(y);
@@ -126,10 +141,12 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < 0.4983f);
-        if (tail) {
+        // about one node in three has a tail point somewhere in the warp:
+        // a warp-uniform branch around the rare per-point tails
+        if (__any_sync(0xffffffffu, tail)) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q], yv[q]);
+                if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q] ^ 0x80000000u, yv[q]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -182,7 +199,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     Real(*s_c)[4] = reinterpret_cast<Real(*)[4]>(smem + L.coef);             // [m][4] boundary (units of K)
     Real(*s_ab)[2] = reinterpret_cast<Real(*)[2]>(smem + L.coef);            // [m][2] paper rule: a_d, b_d
     unsigned char *s_deg = smem + L.deg;                                    // [m] no exercise at the date
-    Node *s_nodes = reinterpret_cast<Node *>(smem + L.nodes);
+    NodeX<Real> *s_nodes = reinterpret_cast<NodeX<Real> *>(smem + L.nodes);
     uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][3]: v_1..v_12 of each dim
     uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift
     R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);              // [slot][128]
@@ -194,6 +211,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     uint32_t gm[kGB];                                                     // all-ones where bit b+1 is set
 #pragma unroll
     for (int b = 0; b < kGB; ++b) gm[b] = 0u - ((g4 >> (b + 1)) & 1u);
+    // FP32: the integers' top bit flipped once here (x - 2^31 as signed values, node_points)
+    const uint32_t flip = FP64 ? 0u : 0x80000000u;
+    unsigned char *const Wt = reinterpret_cast<unsigned char *>(s_W + tid);   // this thread's slot 0
     int cur = -1;
     int m = 0, nslots = 0;
     double vs1 = 0.0, vs2 = 0.0;                                          // this thread's path values (fused modes)
@@ -207,7 +227,27 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             m = J.m;
             nslots = J.nslots;
             const Node *gn = reinterpret_cast<const Node *>(J.nodes);
-            for (int i = tid; i < m; i += kPathgenThreads) s_nodes[i] = gn[i];
+            const double mu = J.r - 0.5 * J.sigma * J.sigma;
+            const Real sqdt = (Real)sqrt(J.dt);
+            // exponent per node: FP32 in base 2 (ex2), FP64 in base e
+            const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
+            constexpr int kSlotBytes = kPathgenThreads * (int)sizeof(R4<Real>);
+            for (int i = tid; i < m; i += kPathgenThreads) {
+                const Node g = gn[i];
+                NodeX<Real> x;
+                x.v4 = 3 * g.coord;
+                x.coord = g.coord;
+                x.wl_o = g.sl * kSlotBytes;
+                x.wr_o = g.sr * kSlotBytes;
+                x.wo_o = g.so * kSlotBytes;
+                x.date = g.date;
+                x.wl = (Real)g.wl;
+                x.wr = (Real)g.wr;
+                x.sd = (Real)g.sdu * sqdt;
+                x.drift = mu_dt * (Real)g.date;
+                x.row = (int64_t)(g.date - 1) * J.ld;
+                s_nodes[i] = x;
+            }
             for (int i = tid; i < 3 * m; i += kPathgenThreads)
                 s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 3) * 32) + (i % 3));
             if (MODE == kPaperRule) {
@@ -229,7 +269,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             }
             cur = jb;
         }
-        for (int k = tid; k < m; k += kPathgenThreads) s_xb[k] = sobol_direct(V, k, base) ^ shift[k];
+        for (int k = tid; k < m; k += kPathgenThreads) s_xb[k] = sobol_direct(V, k, base) ^ shift[k] ^ flip;
         {
             R4<Real> zero;
 #pragma unroll
@@ -241,12 +281,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         const int64_t ld = J.ld;
         const bool store = (int64_t)base + t4 < ld;                       // float4 stays inside the row
         Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + t4;
-        const double mu = J.r - 0.5 * J.sigma * J.sigma;
-        const Real sqdt = (Real)sqrt(J.dt);
+        uint16_t *__restrict__ Sh = reinterpret_cast<uint16_t *>(J.S) + base + t4;
         const Real S0 = MODE == kStore16 ? (Real)(J.S0 * J.invK) : (Real)J.S0;
         const Real off = MODE == kStore16 ? Real(-1) : Real(0);
-        // exponent per node: FP32 in base 2 (ex2), FP64 in base e
-        const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
         const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
         // fused modes: per-path state of the thread's 4 paths
         const bool put = J.type == AMC_PUT;
@@ -275,29 +312,27 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         // (0.442 -> 0.405 ms on 2^20 x 252); FP64 stays rolled (unrolled by 8: 69 -> 106 ms all-FP64 pricing)
 #pragma unroll ((!FP64 && (STORE || MODE == kPaperRule)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
-            const Node nd = s_nodes[n];
-            const uint4 v0 = s_v[3 * nd.coord], v1 = s_v[3 * nd.coord + 1], v2 = s_v[3 * nd.coord + 2];
+            const NodeX<Real> nd = s_nodes[n];
+            const uint4 v0 = s_v[nd.v4], v1 = s_v[nd.v4 + 1], v2 = s_v[nd.v4 + 2];
             const uint32_t vd[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
             uint32_t x0 = s_xb[nd.coord];
 #pragma unroll
             for (int b = 0; b < kGB; ++b) x0 ^= vd[b + 1] & gm[b];
             const uint32_t xq[4] = {x0, x0 ^ v0.x, x0 ^ v0.x ^ v0.y, x0 ^ v0.y};
-            const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
-            const Real drift = mu_dt * (Real)nd.date;
-            const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
-            const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
+            const R4<Real> Wl = *reinterpret_cast<const R4<Real> *>(Wt + nd.wl_o);
+            const R4<Real> Wr = *reinterpret_cast<const R4<Real> *>(Wt + nd.wr_o);
             R4<Real> Wo, So;
-            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, off, Wl, Wr, Wo, So);
-            s_W[nd.so * kPathgenThreads + tid] = Wo;
+            node_points<FP64, Real>(xq, nd.wl, nd.wr, nd.sd, nd.drift, sig, S0, off, Wl, Wr, Wo, So);
+            *reinterpret_cast<R4<Real> *>(Wt + nd.wo_o) = Wo;
             if (MODE == kStore16) {
                 if (store) {
-                    uint16_t *dst = reinterpret_cast<uint16_t *>(J.S) + base + t4 + (int64_t)(nd.date - 1) * ld;
+                    uint16_t *dst = Sh + nd.row;
                     *reinterpret_cast<uint2 *>(dst) = make_uint2(dev::f_to_h2((float)So.v[0], (float)So.v[1]),
                                                                  dev::f_to_h2((float)So.v[2], (float)So.v[3]));
                 }
             } else if (MODE == kStore) {
                 if (store) {
-                    Real *dst = S + (int64_t)(nd.date - 1) * ld;
+                    Real *dst = S + nd.row;
                     if (FP64) {                                           // two 16-byte stores
                         reinterpret_cast<double2 *>(dst)[0] = make_double2((double)So.v[0], (double)So.v[1]);
                         reinterpret_cast<double2 *>(dst)[1] = make_double2((double)So.v[2], (double)So.v[3]);
@@ -453,7 +488,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
                 const uint32_t g = (uint32_t)(j ^ (j >> 1));
                 uint32_t x = 0;
                 for (uint32_t b = 0; b < a.log2M; ++b) x ^= __ldg(Vd + b) & (0u - ((g >> b) & 1u));
-                xq[q] = x;
+                xq[q] = FP64 ? x : x ^ 0x80000000u;              // FP32: top bit flipped (node_points)
             }
             const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
             const Real drift = mu_dt * (Real)nd.date;
