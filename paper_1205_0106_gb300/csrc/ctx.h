@@ -95,8 +95,9 @@ namespace amc {
 struct GroupKey {
     int kind, type, chunks;
     bool lsm;
+    int cubic;                      // cluster sweep: p = 4 (its own kernel variant)
     bool operator==(const GroupKey &o) const {
-        return kind == o.kind && type == o.type && chunks == o.chunks && lsm == o.lsm;
+        return kind == o.kind && type == o.type && chunks == o.chunks && lsm == o.lsm && cubic == o.cubic;
     }
 };
 GroupKey group_key(const amc_option &o, const SweepPlan &pl);

@@ -131,6 +131,7 @@ struct KArgs {
     int32_t max_slots;              // largest bridge stack over the jobs (path generation)
     int32_t jobs_type;              // AMC_PUT / AMC_CALL shared by all jobs of a mixed LSM launch
     int32_t h16;                    // path arrays hold binary16 moneyness (AMC_MIXED16)
+    int32_t jobs_p;                 // basis size shared by all jobs of a cluster-sweep launch
     int64_t total;                  // path-generation tiles over all jobs
     const uint32_t *V;              // direction numbers [AMC_MAX_STEPS][32]
     uint64_t timeout_ns;

@@ -64,7 +64,7 @@ struct alignas(16) NodeX {
     int32_t coord;                // Sobol' dimension
     int32_t wl_o, wr_o, wo_o;     // byte offsets of the left, right and own stack slots
     int32_t date;
-    Real wl, wr, sd, drift;       // bridge weights, sdu sqrt(dt), mu dt date (base 2 in FP32)
+    Real wl, wr, sd, drift;       // bridge weights, sdu sqrt(dt), the exponent's constant (node_points)
     int64_t row;                  // (date - 1) ld: element offset of the date's row
 };
 
@@ -104,14 +104,16 @@ __device__ __forceinline__ int find_job_by_tile(const Job *__restrict__ jobs, in
 }
 
 // The 4 points of one bridge node: z = N^{-1}(u) of the Sobol' integers xq,
-// W = wl W_left + wr W_right + sd z (ref. [13]), S = S0 exp(drift + sig W)
-// + off (Eq. 9 in log space; base 2 in FP32).  off = 0 gives S; S0 / K for
-// S0 and off = -1 give the moneyness y = S/K - 1 with one rounding.  In
-// FP32 xq holds the integers with the top bit flipped, so that as signed
-// values they are x - 2^31 (the uniform's offset from 1/2).
-template <bool FP64, typename Real>
+// W = wl W_left + wr W_right + sd z (ref. [13]), then Eq. 9 in log space:
+// FP64: S = S0 exp(drift + sig W), drift = mu t_d; FP32: base 2 with the
+// spot folded into the exponent, S = 2^(drift + sig W), drift = mu t_d /
+// ln 2 + log2(S0), or (Y16) the moneyness y = 2^(drift + sig W) - 1 with
+// drift = mu t_d / ln 2 + log2(S0 / K).  In FP32 xq holds the integers with
+// the top bit flipped, so that as signed values they are x - 2^31 (the
+// uniform's offset from 1/2).
+template <bool FP64, bool Y16, typename Real>
 __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Real wr, Real sd, Real drift,
-                                            Real sig, Real S0, Real off, const R4<Real> &Wl, const R4<Real> &Wr,
+                                            Real sig, Real S0, const R4<Real> &Wl, const R4<Real> &Wr,
                                             R4<Real> &Wo, R4<Real> &So) {
     if (FP64) {
         Real z[4];
@@ -121,7 +123,7 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
         for (int q = 0; q < 4; ++q) {
             const Real W = fma(sd, z[q], fma(wr, Wr.v[q], wl * Wl.v[q]));
             Wo.v[q] = W;
-            So.v[q] = fma(S0, (Real)exp((double)fma(sig, W, drift)), off);
+            So.v[q] = S0 * (Real)exp((double)fma(sig, W, drift));
         }
     } else {
         // points (0, 1) and (2, 3) as packed pairs: central-region
@@ -140,13 +142,13 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
             z[2 * h + 1] = f2_hi(zc);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < 0.4983f);
-        // about one node in three has a tail point somewhere in the warp:
+        for (int q = 0; q < 4; ++q) tail |= !(fabsf(yv[q]) < kIcdfY0);
+        // about one node in seven has a tail point somewhere in the warp:
         // a warp-uniform branch around the rare per-point tails
         if (__any_sync(0xffffffffu, tail)) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (!(fabsf(yv[q]) < 0.4983f)) z[q] = icdf_tail(xq[q] ^ 0x80000000u, yv[q]);
+                if (!(fabsf(yv[q]) < kIcdfY0)) z[q] = icdf_tail(xq[q] ^ 0x80000000u, yv[q]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -155,8 +157,8 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
                                        f2_mul(f2_splat((float)wl),
                                               f2_pack((float)Wl.v[2 * h], (float)Wl.v[2 * h + 1]))));
             const f2 e = f2_fma(f2_splat((float)sig), W, f2_splat((float)drift));
-            const f2 Sv = f2_fma(f2_splat((float)S0), f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e))),
-                                 f2_splat((float)off));
+            f2 Sv = f2_pack(ex2_approx(f2_lo(e)), ex2_approx(f2_hi(e)));
+            if (Y16) Sv = f2_add(Sv, f2_splat(-1.f));
             Wo.v[2 * h] = (Real)f2_lo(W);
             Wo.v[2 * h + 1] = (Real)f2_hi(W);
             So.v[2 * h] = (Real)f2_lo(Sv);
@@ -230,7 +232,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             const double mu = J.r - 0.5 * J.sigma * J.sigma;
             const Real sqdt = (Real)sqrt(J.dt);
             // exponent per node: FP32 in base 2 (ex2), FP64 in base e
-            const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
+            const Real mu_dt = (Real)(mu * J.dt);                              // FP64
+            const double mu_dt2 = mu * J.dt * 1.4426950408889634;                 // FP32: base 2
+            const double lS0 = log2(MODE == kStore16 ? J.S0 * J.invK : J.S0);
             constexpr int kSlotBytes = kPathgenThreads * (int)sizeof(R4<Real>);
             for (int i = tid; i < m; i += kPathgenThreads) {
                 const Node g = gn[i];
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
                 x.wl = (Real)g.wl;
                 x.wr = (Real)g.wr;
                 x.sd = (Real)g.sdu * sqdt;
-                x.drift = mu_dt * (Real)g.date;
+                x.drift = FP64 ? mu_dt * (Real)g.date : (Real)(mu_dt2 * (double)g.date + lS0);
                 x.row = (int64_t)(g.date - 1) * J.ld;
                 s_nodes[i] = x;
             }
@@ -282,8 +286,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         const bool store = (int64_t)base + t4 < ld;                       // float4 stays inside the row
         Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + t4;
         uint16_t *__restrict__ Sh = reinterpret_cast<uint16_t *>(J.S) + base + t4;
-        const Real S0 = MODE == kStore16 ? (Real)(J.S0 * J.invK) : (Real)J.S0;
-        const Real off = MODE == kStore16 ? Real(-1) : Real(0);
+        const Real S0 = (Real)J.S0;                                      // FP64 (FP32: in the drift)
         const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
         // fused modes: per-path state of the thread's 4 paths
         const bool put = J.type == AMC_PUT;
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             const R4<Real> Wl = *reinterpret_cast<const R4<Real> *>(Wt + nd.wl_o);
             const R4<Real> Wr = *reinterpret_cast<const R4<Real> *>(Wt + nd.wr_o);
             R4<Real> Wo, So;
-            node_points<FP64, Real>(xq, nd.wl, nd.wr, nd.sd, nd.drift, sig, S0, off, Wl, Wr, Wo, So);
+            node_points<FP64, MODE == kStore16, Real>(xq, nd.wl, nd.wr, nd.sd, nd.drift, sig, S0, Wl, Wr, Wo, So);
             *reinterpret_cast<R4<Real> *>(Wt + nd.wo_o) = Wo;
             if (MODE == kStore16) {
                 if (store) {
@@ -458,7 +461,8 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
     const double mu = J.r - 0.5 * J.sigma * J.sigma;
     const Real sqdt = (Real)sqrt(J.dt);
     const Real S0 = (Real)J.S0;
-    const Real mu_dt = FP64 ? (Real)(mu * J.dt) : (Real)(mu * J.dt * 1.4426950408889634);
+    const Real mu_dt = (Real)(mu * J.dt);                                  // FP64
+    const double mu_dt2 = mu * J.dt * 1.4426950408889634, lS0 = log2(J.S0);   // FP32: base 2, spot folded in
     const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
         const uint64_t base = (uint64_t)tile * kTilePoints;
@@ -491,11 +495,11 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
                 xq[q] = FP64 ? x : x ^ 0x80000000u;              // FP32: top bit flipped (node_points)
             }
             const Real wl = (Real)nd.wl, wr = (Real)nd.wr, sd = (Real)nd.sdu * sqdt;
-            const Real drift = mu_dt * (Real)nd.date;
+            const Real drift = FP64 ? mu_dt * (Real)nd.date : (Real)(mu_dt2 * (double)nd.date + lS0);
             const R4<Real> Wl = s_W[nd.sl * kPathgenThreads + tid];
             const R4<Real> Wr = s_W[nd.sr * kPathgenThreads + tid];
             R4<Real> Wo, So;
-            node_points<FP64, Real>(xq, wl, wr, sd, drift, sig, S0, Real(0), Wl, Wr, Wo, So);
+            node_points<FP64, false, Real>(xq, wl, wr, sd, drift, sig, S0, Wl, Wr, Wo, So);
             s_W[nd.so * kPathgenThreads + tid] = Wo;
             if (store) {
                 Real *dst = S + (int64_t)(nd.date - 1) * ld;

@@ -472,6 +472,7 @@ int run_batch(amc_ctx *c, const amc_option *opts, int n, int prec, bool greeks, 
         if (a.key.type != b.key.type) return a.key.type < b.key.type;
         if (a.key.chunks != b.key.chunks) return a.key.chunks < b.key.chunks;
         if (a.key.lsm != b.key.lsm) return a.key.lsm && !b.key.lsm;
+        if (a.key.cubic != b.key.cubic) return a.key.cubic < b.key.cubic;
         return opts[a.idx].n_steps > opts[b.idx].n_steps;
     });
     if (out)
@@ -625,6 +626,7 @@ GroupKey group_key(const amc_option &o, const SweepPlan &pl) {
     k.type = pl.kind >= 2 ? o.type : 0;
     k.chunks = pl.kind == 3 ? pl.ctas : pl.chunks;    // one cluster size per cluster launch
     k.lsm = o.rule == AMC_RULE_LSM;
+    k.cubic = (pl.kind == 3 && o.basis == 4) ? 1 : 0;
     return k;
 }
 
@@ -735,6 +737,7 @@ int launch_group(amc_ctx *c, const amc_option *const *opts, const SweepPlan *pla
     a.max_m = max_m;
     a.max_slots = max_slots;
     a.jobs_type = opts[0]->type;
+    a.jobs_p = opts[0]->basis;
     a.total = tiles;
     a.V = c->V;
     a.h16 = prec == AMC_MIXED16 ? 1 : 0;

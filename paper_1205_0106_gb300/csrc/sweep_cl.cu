@@ -271,7 +271,9 @@ __device__ __noinline__ dfl cl_gram_inverse(dfl Mq, int p, int lane, bool &deg) 
     return in ? xn : df_of(0.f);
 }
 
-template <bool PUT, bool H16>
+// P4: the cubic basis (p = 4); otherwise p <= 3.  Every option of a launch
+// has the same kind (batches are grouped by it).
+template <bool PUT, bool H16, bool P4>
 __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__ KArgs a) {
     using E = typename std::conditional<H16, uint16_t, float>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -281,6 +283,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
     const Job &J = a.jobs ? a.jobs[jb] : a.one;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = J.m, p = J.p;
+    if (P4 != (p == 4)) {            // the launch chose the other variant: every CTA of the cluster leaves here
+        if (tid == 0 && lc == 0) atomicCAS(J.status, 0, AMC_EINVAL);
+        return;
+    }
     const float invK = (float)J.invK, disc = (float)J.disc;
     const E *__restrict__ S = reinterpret_cast<const E *>(J.S);
     const int64_t N = J.N, ld = J.ld;
@@ -407,241 +413,259 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
             bar_arrive_beta();                                // path warps waiting for a beta see the abort
         }
     } else {
-        // ================================================== path warps
-        // thread t = tid - 32 owns register pairs t + 992 s (s = 0..7), and,
-        // for t < 512, the one path 15872 + t whose cash flow is in shared memory
-        const int t = tid - 32;
-        auto pidx = [&](int i) { return 2 * (t + kPathThreads * (i >> 1)) + (i & 1); };
-        const int xidx = kRegPaths + t;
-        const bool has_x = t < kPPC - kRegPaths;
-        if (t == 0)
-            for (int d = m; d >= 1 && d > m - kSlots; --d) issue(d);
-        float cf[kPPT];
-        bool stop = !wait_bar(&sm.mbar[m % kSlots], slot_parity(m), false);
-        if (!stop) {
-            const E *sl = sm.S[m % kSlots];
-#pragma unroll
-            for (int i = 0; i < kPPT; ++i) {
-                const int idx = pidx(i);
-                const float y = raw_y(sl, idx, invK);
-                const float h = PUT ? -y : y;
-                cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
-            }
-            if (has_x) {
-                const float y = raw_y(sl, xidx, invK);
-                const float h = PUT ? -y : y;
-                sm.cfx[t] = (xidx < nloc && h > 0.f) ? h : 0.f;
-            }
-        }
-        // Gram pass of date e over all paths of the CTA: y in place (0 off
-        // the money), the 7 moments.  The in-the-money indicator is
-        // I = sat(-y 2^100) for a put, sat(y 2^100) for a call: exactly 1 for
-        // every y of the money's sign, since a nonzero FP32 y of
-        // fma(S, fl(1/K), -1) has |y| >= 2^-48, and 0 otherwise; then y I is
-        // the in-place value and I the count (multiplies on the FMA pipe
-        // instead of compares and selects)
-        auto gram = [&](int e) -> bool {
-            if (!wait_bar(&sm.mbar[e % kSlots], slot_parity(e), false)) return false;
-            E *sl = sm.S[e % kSlots];
-            const f2 z2 = f2_splat(0.f);
-            const float big = PUT ? -0x1p100f : 0x1p100f;
-            f2 g0 = z2, g1 = z2, g2 = z2, g3 = z2, g4 = z2, g5 = z2, g6 = z2;
-            auto pair = [&](int idx, bool tail) {
-                const f2 Yr = raw_y2(sl, idx, invK);
-                float ilo = __saturatef(f2_lo(Yr) * big), ihi = __saturatef(f2_hi(Yr) * big);
-                f2 Y;
-                if (tail) {
-                    // the last CTA's slot holds no paths beyond nloc (nor copied
-                    // bytes beyond the row's end): select, never multiply, there
-                    const bool v0 = idx < nloc, v1 = idx + 1 < nloc;
-                    ilo = v0 ? ilo : 0.f;
-                    ihi = v1 ? ihi : 0.f;
-                    Y = f2_pack(v0 ? f2_lo(Yr) * ilo : 0.f, v1 ? f2_hi(Yr) * ihi : 0.f);
-                } else {
-                    Y = f2_mul(Yr, f2_pack(ilo, ihi));
-                }
-                const f2 I = f2_pack(ilo, ihi);
-                put_y2(sl, idx, Y);
-                g0 = f2_add(g0, I);
-                const f2 YY = f2_mul(Y, Y), Y3 = f2_mul(YY, Y);
-                g1 = f2_add(g1, Y);
-                g2 = f2_add(g2, YY);
-                g3 = f2_add(g3, Y3);
-                g4 = f2_fma(YY, YY, g4);
-                g5 = f2_fma(YY, Y3, g5);
-                g6 = f2_fma(Y3, Y3, g6);
-            };
-            // pairs t + 992 s: s = 0..7 for every path thread, s = 8 for t < 256
-            constexpr int kFullRounds = kPairs / kPathThreads;           // 8
-            if (nloc == kPPC) {
-#pragma unroll
-                for (int s2 = 0; s2 < kFullRounds; ++s2) pair(2 * (t + kPathThreads * s2), false);
-                if (t + kPathThreads * kFullRounds < kPairs) pair(2 * (t + kPathThreads * kFullRounds), false);
-            } else {
-#pragma unroll 2
-                for (int q = t; q < kPairs; q += kPathThreads) pair(2 * q, true);
-            }
-            fence_proxy_async();         // these generic writes precede a later TMA refill
-            const float g[8] = {f2_lo(g0) + f2_hi(g0), f2_lo(g1) + f2_hi(g1), f2_lo(g2) + f2_hi(g2),
-                                f2_lo(g3) + f2_hi(g3), f2_lo(g4) + f2_hi(g4), f2_lo(g5) + f2_hi(g5),
-                                f2_lo(g6) + f2_hi(g6), 0.f};
-            const float r = warp_sum8(g, lane);
-            const int k = (lane >> 2) & 7;
-            if ((lane & 3) == 0 && k < 7) sm.redM[e & 1][warp - 1][k] = r;
-            return true;
-        };
-        auto send_gram = [&](int e) {    // after the path-warp barrier that completes redM[e & 1]
-            const int v = warp - 5;
-            if (v >= 0 && v < 7) {
-                const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redM[e & 1][lane][v] : 0.f));
-                if (lane < G && inject_date != e + 1) {
-                    send_df(map_to(saddr(&sm.recvM[e % 3][v][lc]), (uint32_t)lane),
-                            map_to(saddr(&sm.xbarM[e % 3]), (uint32_t)lane), tot.hi, tot.lo);
-                }
-            }
-        };
-        if (!stop && m >= 2) stop = !gram(m - 1);
-        stop = bar_paths_any(stop || sm.abort);
-        if (!stop && m >= 2) send_gram(m - 1);
-
-        for (int d = m - 1; d >= 1 && !stop; --d) {
-            const int par = d & 1;
-            bar_sync_beta();                                  // beta_{d+1} from the solver warp
-            if (sm.abort) {
-                stop = true;
-                break;
-            }
-            // exercise at d+1, discount to t_d, right-hand sides of date d.
-            // With y in place (0 off the money) the exercise test
-            // "in the money and h > c(y)" is h > max(c(y), 0), h = -y (put)
-            // or y (call); the in-the-money indicator of the date-d sums is
-            // sat(-+y 2^100) as in the Gram pass
-            {
-                const int pe = (d + 1) & 1;
-                const bool ex = d + 1 <= m - 1 && !sm.deg[pe];
-                const float b0 = sm.beta[pe][0], b1 = sm.beta[pe][1], b2 = sm.beta[pe][2], b3 = sm.beta[pe][3];
-                const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
-                const f2 DISC = f2_splat(disc), z2 = f2_splat(0.f), SG = f2_splat(PUT ? -1.f : 1.f);
-                const E *se = sm.S[(d + 1) % kSlots];
-                const E *sr = sm.S[d % kSlots];
-                f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
-#pragma unroll
-                for (int i = 0; i < kPPT; i += 2) {
+        // The cubic basis (P4: moments up to y^6, right-hand sides up to y^3 C)
+        // or p <= 3 (y^4 and y^2 C at most) is a compile-time choice.
+        auto path_warps = [&](auto Q) {
+            // ================================================== path warps
+            // thread t = tid - 32 owns register pairs t + 992 s (s = 0..7), and,
+            // for t < 512, the one path 15872 + t whose cash flow is in shared memory
+            const int t = tid - 32;
+            auto pidx = [&](int i) { return 2 * (t + kPathThreads * (i >> 1)) + (i & 1); };
+            const int xidx = kRegPaths + t;
+            const bool has_x = t < kPPC - kRegPaths;
+            if (t == 0)
+                for (int d = m; d >= 1 && d > m - kSlots; --d) issue(d);
+            float cf[kPPT];
+            bool stop = !wait_bar(&sm.mbar[m % kSlots], slot_parity(m), false);
+            if (!stop) {
+                const E *sl = sm.S[m % kSlots];
+    #pragma unroll
+                for (int i = 0; i < kPPT; ++i) {
                     const int idx = pidx(i);
-                    if (ex) {
-                        const f2 Y = y2_at(se, idx);
-                        const f2 C = f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0);
-                        const f2 H = f2_mul(Y, SG);
-                        const float hl = f2_lo(H), hh = f2_hi(H);
-                        cf[i] = hl > fmaxf(f2_lo(C), 0.f) ? hl : cf[i];
-                        cf[i + 1] = hh > fmaxf(f2_hi(C), 0.f) ? hh : cf[i + 1];
-                    }
-                    const f2 Y = y2_at(sr, idx);
-                    const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
-                    cf[i] = f2_lo(C);
-                    cf[i + 1] = f2_hi(C);
-                    const float big = PUT ? -0x1p100f : 0x1p100f;
-                    R0 = f2_fma(C, f2_pack(__saturatef(f2_lo(Y) * big), __saturatef(f2_hi(Y) * big)), R0);
-                    const f2 YY = f2_mul(Y, Y);
-                    R1 = f2_fma(C, Y, R1);                            // y = 0 off the money
-                    R2 = f2_fma(C, YY, R2);
-                    R3 = f2_fma(C, f2_mul(YY, Y), R3);
+                    const float y = raw_y(sl, idx, invK);
+                    const float h = PUT ? -y : y;
+                    cf[i] = (idx < nloc && h > 0.f) ? h : 0.f;
                 }
-                float rr[4] = {f2_lo(R0) + f2_hi(R0), f2_lo(R1) + f2_hi(R1), f2_lo(R2) + f2_hi(R2),
-                               f2_lo(R3) + f2_hi(R3)};
-                if (has_x) {                                          // the shared-memory path
-                    float c = sm.cfx[t];
-                    if (ex) {
+                if (has_x) {
+                    const float y = raw_y(sl, xidx, invK);
+                    const float h = PUT ? -y : y;
+                    sm.cfx[t] = (xidx < nloc && h > 0.f) ? h : 0.f;
+                }
+            }
+            // Gram pass of date e over all paths of the CTA: y in place (0 off
+            // the money), the 7 moments.  The in-the-money indicator is
+            // I = sat(-y 2^100) for a put, sat(y 2^100) for a call: exactly 1 for
+            // every y of the money's sign, since a nonzero FP32 y of
+            // fma(S, fl(1/K), -1) has |y| >= 2^-48, and 0 otherwise; then y I is
+            // the in-place value and I the count (multiplies on the FMA pipe
+            // instead of compares and selects)
+            auto gram = [&](int e) -> bool {
+                if (!wait_bar(&sm.mbar[e % kSlots], slot_parity(e), false)) return false;
+                E *sl = sm.S[e % kSlots];
+                const f2 z2 = f2_splat(0.f);
+                const float big = PUT ? -0x1p100f : 0x1p100f;
+                f2 g0 = z2, g1 = z2, g2 = z2, g3 = z2, g4 = z2, g5 = z2, g6 = z2;
+                // P4: the cubic basis (moments up to y^6); otherwise p <= 3 needs y^4 at most
+                auto pair = [&](int idx, bool tail, auto P4) {
+                    const f2 Yr = raw_y2(sl, idx, invK);
+                    float ilo = __saturatef(f2_lo(Yr) * big), ihi = __saturatef(f2_hi(Yr) * big);
+                    f2 Y;
+                    if (tail) {
+                        // the last CTA's slot holds no paths beyond nloc (nor copied
+                        // bytes beyond the row's end): select, never multiply, there
+                        const bool v0 = idx < nloc, v1 = idx + 1 < nloc;
+                        ilo = v0 ? ilo : 0.f;
+                        ihi = v1 ? ihi : 0.f;
+                        Y = f2_pack(v0 ? f2_lo(Yr) * ilo : 0.f, v1 ? f2_hi(Yr) * ihi : 0.f);
+                    } else {
+                        Y = f2_mul(Yr, f2_pack(ilo, ihi));
+                    }
+                    const f2 I = f2_pack(ilo, ihi);
+                    put_y2(sl, idx, Y);
+                    g0 = f2_add(g0, I);
+                    const f2 YY = f2_mul(Y, Y), Y3 = f2_mul(YY, Y);
+                    g1 = f2_add(g1, Y);
+                    g2 = f2_add(g2, YY);
+                    g3 = f2_add(g3, Y3);
+                    g4 = f2_fma(YY, YY, g4);
+                    if constexpr (decltype(P4)::value) {
+                        g5 = f2_fma(YY, Y3, g5);
+                        g6 = f2_fma(Y3, Y3, g6);
+                    }
+                };
+                // pairs t + 992 s: s = 0..7 for every path thread, s = 8 for t < 256
+                constexpr int kFullRounds = kPairs / kPathThreads;           // 8
+                auto all_pairs = [&](auto P4) {
+                    if (nloc == kPPC) {
+    #pragma unroll
+                        for (int s2 = 0; s2 < kFullRounds; ++s2) pair(2 * (t + kPathThreads * s2), false, P4);
+                        if (t + kPathThreads * kFullRounds < kPairs)
+                            pair(2 * (t + kPathThreads * kFullRounds), false, P4);
+                    } else {
+    #pragma unroll 2
+                        for (int q = t; q < kPairs; q += kPathThreads) pair(2 * q, true, P4);
+                    }
+                };
+                all_pairs(Q);
+                fence_proxy_async();         // these generic writes precede a later TMA refill
+                const float g[8] = {f2_lo(g0) + f2_hi(g0), f2_lo(g1) + f2_hi(g1), f2_lo(g2) + f2_hi(g2),
+                                    f2_lo(g3) + f2_hi(g3), f2_lo(g4) + f2_hi(g4), f2_lo(g5) + f2_hi(g5),
+                                    f2_lo(g6) + f2_hi(g6), 0.f};
+                const float r = warp_sum8(g, lane);
+                const int k = (lane >> 2) & 7;
+                if ((lane & 3) == 0 && k < 7) sm.redM[e & 1][warp - 1][k] = r;
+                return true;
+            };
+            auto send_gram = [&](int e) {    // after the path-warp barrier that completes redM[e & 1]
+                const int v = warp - 5;
+                if (v >= 0 && v < 7) {
+                    const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redM[e & 1][lane][v] : 0.f));
+                    if (lane < G && inject_date != e + 1) {
+                        send_df(map_to(saddr(&sm.recvM[e % 3][v][lc]), (uint32_t)lane),
+                                map_to(saddr(&sm.xbarM[e % 3]), (uint32_t)lane), tot.hi, tot.lo);
+                    }
+                }
+            };
+            if (!stop && m >= 2) stop = !gram(m - 1);
+            stop = bar_paths_any(stop || sm.abort);
+            if (!stop && m >= 2) send_gram(m - 1);
+
+            for (int d = m - 1; d >= 1 && !stop; --d) {
+                const int par = d & 1;
+                bar_sync_beta();                                  // beta_{d+1} from the solver warp
+                if (sm.abort) {
+                    stop = true;
+                    break;
+                }
+                // exercise at d+1, discount to t_d, right-hand sides of date d.
+                // With y in place (0 off the money) the exercise test
+                // "in the money and h > c(y)" is h > max(c(y), 0), h = -y (put)
+                // or y (call); the in-the-money indicator of the date-d sums is
+                // sat(-+y 2^100) as in the Gram pass
+                {
+                    const int pe = (d + 1) & 1;
+                    const bool ex = d + 1 <= m - 1 && !sm.deg[pe];
+                    const float b0 = sm.beta[pe][0], b1 = sm.beta[pe][1], b2 = sm.beta[pe][2], b3 = sm.beta[pe][3];
+                    const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
+                    const f2 DISC = f2_splat(disc), z2 = f2_splat(0.f), SG = f2_splat(PUT ? -1.f : 1.f);
+                    const E *se = sm.S[(d + 1) % kSlots];
+                    const E *sr = sm.S[d % kSlots];
+                    f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
+                    // P4: the cubic basis; otherwise b3 = 0 and R3 is not used (p <= 3)
+                    auto ex_rhs = [&](auto P4) {
+                        constexpr bool Q4 = decltype(P4)::value;
+    #pragma unroll
+                    for (int i = 0; i < kPPT; i += 2) {
+                        const int idx = pidx(i);
+                        if (ex) {
+                            const f2 Y = y2_at(se, idx);
+                            const f2 C = Q4 ? f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0)
+                                            : f2_fma(f2_fma(B2, Y, B1), Y, B0);
+                            const f2 H = f2_mul(Y, SG);
+                            const float hl = f2_lo(H), hh = f2_hi(H);
+                            cf[i] = hl > fmaxf(f2_lo(C), 0.f) ? hl : cf[i];
+                            cf[i + 1] = hh > fmaxf(f2_hi(C), 0.f) ? hh : cf[i + 1];
+                        }
+                        const f2 Y = y2_at(sr, idx);
+                        const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
+                        cf[i] = f2_lo(C);
+                        cf[i + 1] = f2_hi(C);
+                        const float big = PUT ? -0x1p100f : 0x1p100f;
+                        R0 = f2_fma(C, f2_pack(__saturatef(f2_lo(Y) * big), __saturatef(f2_hi(Y) * big)), R0);
+                        const f2 YY = f2_mul(Y, Y);
+                        R1 = f2_fma(C, Y, R1);                            // y = 0 off the money
+                        R2 = f2_fma(C, YY, R2);
+                        if (Q4) R3 = f2_fma(C, f2_mul(YY, Y), R3);
+                    }
+                    };
+                    ex_rhs(Q);
+                    float rr[4] = {f2_lo(R0) + f2_hi(R0), f2_lo(R1) + f2_hi(R1), f2_lo(R2) + f2_hi(R2),
+                                   f2_lo(R3) + f2_hi(R3)};
+                    if (has_x) {                                          // the shared-memory path
+                        float c = sm.cfx[t];
+                        if (ex) {
+                            const float y = y_at(se, xidx);
+                            const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+                            const float h = PUT ? -y : y;
+                            c = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : c;
+                        }
+                        c *= disc;
+                        sm.cfx[t] = c;
+                        const float y = y_at(sr, xidx);
+                        const float cc = y != 0.f ? c : 0.f, yy = y * y;
+                        rr[0] += cc;
+                        rr[1] = fmaf(c, y, rr[1]);
+                        rr[2] = fmaf(c, yy, rr[2]);
+                        rr[3] = fmaf(c, yy * y, rr[3]);
+                    }
+                    const float r = warp_sum4(rr, lane);
+                    const int k = (lane >> 3) & 3;
+                    if ((lane & 7) == 0) sm.redR[par][warp - 1][k] = k < p ? r : 0.f;
+                }
+                stop = bar_paths_any(sm.abort);                       // partials complete; slot d+1 free
+                if (stop) break;
+                if (t == 0 && d - 2 >= 1) issue(d - 2);                   // into the slot of date d+1
+                {
+                    const int v = warp - 1;                               // warps 1..4: right-hand side v
+                    if (v < 4) {
+                        const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redR[par][lane][v] : 0.f));
+                        if (lane < G && inject_date != d) {
+                            send_df(map_to(saddr(&sm.recvR[par][v][lc]), (uint32_t)lane),
+                                    map_to(saddr(&sm.xbarR[par]), (uint32_t)lane), tot.hi, tot.lo);
+                        }
+                    }
+                }
+                // Gram pass of date d-1 while the exchange and the solve run
+                if (d - 1 >= 1) {
+                    bool ok = gram(d - 1);
+                    stop = bar_paths_any(!ok || sm.abort);
+                    if (stop) break;
+                    send_gram(d - 1);
+                }
+            }
+            // the last exercise date, t_1
+            if (!stop && m >= 2) {
+                bar_sync_beta();
+                if (sm.abort) {
+                    stop = true;
+                } else if (!sm.deg[1]) {
+                    const float b0 = sm.beta[1][0], b1 = sm.beta[1][1], b2 = sm.beta[1][2], b3 = sm.beta[1][3];
+                    const E *se = sm.S[1 % kSlots];
+    #pragma unroll
+                    for (int i = 0; i < kPPT; ++i) {
+                        const float y = y_at(se, pidx(i));
+                        const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
+                        const float h = PUT ? -y : y;
+                        cf[i] = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : cf[i];
+                    }
+                    if (has_x) {
                         const float y = y_at(se, xidx);
                         const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
                         const float h = PUT ? -y : y;
-                        c = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : c;
-                    }
-                    c *= disc;
-                    sm.cfx[t] = c;
-                    const float y = y_at(sr, xidx);
-                    const float cc = y != 0.f ? c : 0.f, yy = y * y;
-                    rr[0] += cc;
-                    rr[1] = fmaf(c, y, rr[1]);
-                    rr[2] = fmaf(c, yy, rr[2]);
-                    rr[3] = fmaf(c, yy * y, rr[3]);
-                }
-                const float r = warp_sum4(rr, lane);
-                const int k = (lane >> 3) & 3;
-                if ((lane & 7) == 0) sm.redR[par][warp - 1][k] = k < p ? r : 0.f;
-            }
-            stop = bar_paths_any(sm.abort);                       // partials complete; slot d+1 free
-            if (stop) break;
-            if (t == 0 && d - 2 >= 1) issue(d - 2);                   // into the slot of date d+1
-            {
-                const int v = warp - 1;                               // warps 1..4: right-hand side v
-                if (v < 4) {
-                    const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redR[par][lane][v] : 0.f));
-                    if (lane < G && inject_date != d) {
-                        send_df(map_to(saddr(&sm.recvR[par][v][lc]), (uint32_t)lane),
-                                map_to(saddr(&sm.xbarR[par]), (uint32_t)lane), tot.hi, tot.lo);
+                        if ((PUT ? y < 0.f : y > 0.f) && h > cont) sm.cfx[t] = h;
                     }
                 }
             }
-            // Gram pass of date d-1 while the exchange and the solve run
-            if (d - 1 >= 1) {
-                bool ok = gram(d - 1);
-                stop = bar_paths_any(!ok || sm.abort);
-                if (stop) break;
-                send_gram(d - 1);
-            }
-        }
-        // the last exercise date, t_1
-        if (!stop && m >= 2) {
-            bar_sync_beta();
-            if (sm.abort) {
-                stop = true;
-            } else if (!sm.deg[1]) {
-                const float b0 = sm.beta[1][0], b1 = sm.beta[1][1], b2 = sm.beta[1][2], b3 = sm.beta[1][3];
-                const E *se = sm.S[1 % kSlots];
-#pragma unroll
+            // final per-thread sums (units of K): CF, CF^2
+            float fs[4] = {0.f, 0.f, 0.f, 0.f};
+            if (!stop) {
+    #pragma unroll
                 for (int i = 0; i < kPPT; ++i) {
-                    const float y = y_at(se, pidx(i));
-                    const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
-                    const float h = PUT ? -y : y;
-                    cf[i] = ((PUT ? y < 0.f : y > 0.f) && h > cont) ? h : cf[i];
+                    if (pidx(i) >= nloc) continue;
+                    fs[0] += cf[i];
+                    fs[1] += cf[i] * cf[i];
                 }
-                if (has_x) {
-                    const float y = y_at(se, xidx);
-                    const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
-                    const float h = PUT ? -y : y;
-                    if ((PUT ? y < 0.f : y > 0.f) && h > cont) sm.cfx[t] = h;
+                if (has_x && xidx < nloc) {
+                    const float c = sm.cfx[t];
+                    fs[0] += c;
+                    fs[1] += c * c;
                 }
             }
-        }
-        // final per-thread sums (units of K): CF, CF^2
-        float fs[4] = {0.f, 0.f, 0.f, 0.f};
-        if (!stop) {
-#pragma unroll
-            for (int i = 0; i < kPPT; ++i) {
-                if (pidx(i) >= nloc) continue;
-                fs[0] += cf[i];
-                fs[1] += cf[i] * cf[i];
-            }
-            if (has_x && xidx < nloc) {
-                const float c = sm.cfx[t];
-                fs[0] += c;
-                fs[1] += c * c;
-            }
-        }
-        const float r = warp_sum4(fs, lane);
-        const int k = (lane >> 3) & 3;
-        if ((lane & 7) == 0) sm.redF[warp - 1][k] = r;
-        if (stop && t == 0) {
-            // bounded wait for this CTA's own copies still in flight
-            for (int s = 0; s < kSlots; ++s) {
-                const int d = sm.pend[s];
-                if (d <= 0) continue;
-                const uint64_t t0 = globaltimer();
-                while (!mbar_test(&sm.mbar[s], slot_parity(d)) && globaltimer() - t0 < timeout_ns) {
+            const float r = warp_sum4(fs, lane);
+            const int k = (lane >> 3) & 3;
+            if ((lane & 7) == 0) sm.redF[warp - 1][k] = r;
+            if (stop && t == 0) {
+                // bounded wait for this CTA's own copies still in flight
+                for (int s = 0; s < kSlots; ++s) {
+                    const int d = sm.pend[s];
+                    if (d <= 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_test(&sm.mbar[s], slot_parity(d)) && globaltimer() - t0 < timeout_ns) {
+                    }
                 }
             }
-        }
+        };
+        path_warps(std::integral_constant<bool, P4>{});
     }
     __syncthreads();
     if (!sm.abort) {
@@ -673,8 +697,14 @@ size_t sweep_cl_smem() { return sizeof(SmemCl<float>); }
 cudaError_t launch_sweep_cl(const KArgs &a, int cluster, int n_clusters, cudaStream_t st) {
     if (cluster < 1 || cluster > kMaxG || n_clusters < 1) return cudaErrorInvalidValue;
     const bool put = (a.jobs ? a.jobs_type : a.one.type) == AMC_PUT;
-    void (*kern)(KArgs) = a.h16 ? (put ? sweep_cl_kernel<true, true> : sweep_cl_kernel<false, true>)
-                                : (put ? sweep_cl_kernel<true, false> : sweep_cl_kernel<false, false>);
+    const bool p4 = (a.jobs ? a.jobs_p : a.one.p) == 4;
+    void (*kern)(KArgs);
+    if (p4)
+        kern = a.h16 ? (put ? sweep_cl_kernel<true, true, true> : sweep_cl_kernel<false, true, true>)
+                     : (put ? sweep_cl_kernel<true, false, true> : sweep_cl_kernel<false, false, true>);
+    else
+        kern = a.h16 ? (put ? sweep_cl_kernel<true, true, false> : sweep_cl_kernel<false, true, false>)
+                     : (put ? sweep_cl_kernel<true, false, false> : sweep_cl_kernel<false, false, false>);
     const void *f = (const void *)kern;
     const size_t smem = a.h16 ? sizeof(SmemCl<uint16_t>) : sizeof(SmemCl<float>);
     cudaError_t e = ensure_smem(f, smem);
@@ -704,16 +734,16 @@ cudaError_t launch_sweep_cl(const KArgs &a, int cluster, int n_clusters, cudaStr
 // ring is smaller, so the binary16 variants hold at least as many.
 cudaError_t sweep_cl_max_cluster(int *out) {
     *out = 0;
-    const void *f = (const void *)sweep_cl_kernel<true, false>;
+    const void *f = (const void *)sweep_cl_kernel<true, false, true>;
     const size_t smem = sizeof(SmemCl<float>);
     cudaError_t e = ensure_smem(f, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)sweep_cl_kernel<false, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                             1);
+    e = cudaFuncSetAttribute((const void *)sweep_cl_kernel<false, false, true>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    e = ensure_smem((const void *)sweep_cl_kernel<false, false>, smem);
+    e = ensure_smem((const void *)sweep_cl_kernel<false, false, true>, smem);
     if (e != cudaSuccess) return e;
     for (int g = kMaxG; g >= 1; --g) {
         cudaLaunchConfig_t cfg = {};

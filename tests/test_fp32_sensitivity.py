@@ -85,3 +85,15 @@ def test_binary16_moneyness_rounding_moves_an_unstable_batch_option_beyond_the_b
     o = workloads.scaled(workloads.batch_options()[2], n_paths=2 ** 14)
     assert o.type == 1 and o.basis == 3
     assert binary16_shift(o) > 2e-4
+
+
+def test_many_dates_on_few_paths_are_sensitive_to_fp32_path_noise():
+    """512 exercise dates on 3000 paths (the parity table's max_dates put,
+    basis 3): relative path noise of 2e-5, the FP32 paths' error level, moves
+    the oracle's own price by more than half the 2e-4 K bar (2.0e-4 K over
+    four draws), while FP32 sums on identical paths do not (2e-7 K).  The
+    free-running mixed price of this case is therefore held to the replay
+    check when it misses the bar (check_mixed_vs_oracle)."""
+    o = workloads.Option(100.0, 90.0, 0.05, 0.2, 1.0, 512, 3000, basis=3, seed=16)
+    assert path_noise_spread(o) > 1e-4
+    assert fp32_sum_shift(o) < 1e-5

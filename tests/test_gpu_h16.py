@@ -5,8 +5,9 @@ The path array holds y = S/K - 1 in IEEE binary16 instead of S in FP32
 cluster sweep, the L2-exchange sweep and the streaming sweep of large
 options) read it.  Bars:
   paths        within one binary16 unit in the last place of the FP32
-               path's moneyness (plus 4 FP32 roundings), and within that
-               plus the FP32 paths' 2e-5 of the oracle's FP64 paths
+               path's moneyness plus the FP32 roundings of the two paths'
+               exponents, and within a binary16 unit plus the FP32 paths'
+               2e-5 of the oracle's FP64 paths
   sweep        on its own binary16 paths: the replay check (every date's
                normal equations and the price within the FP32 bounds of the
                kernel's arithmetic, tests/lsm_replay.py), and within 2e-4 K
@@ -57,6 +58,12 @@ def _ulp16(y):
     return 2.0 ** (e - 10)
 
 
+def _ulp32(v):
+    """Spacing of FP32 numbers at |v| (at least 2^-126)."""
+    e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** -126)))
+    return 2.0 ** (e - 23)
+
+
 def _gpu_price(amc, ctx, o, prec):
     return amc.amc_price_american(ctx, o.S0, o.K, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.basis, o.type, o.seed,
                                   o.rule, prec)
@@ -84,11 +91,17 @@ def test_binary16_paths_are_the_fp32_paths_rounded(amc, ctx, torch, name, o):
     amc.amc_generate_paths(ctx, o, amc.AMC_MIXED, S32)
     amc.amc_generate_paths(ctx, o, amc.AMC_MIXED16, Y16)
     torch.cuda.synchronize()
-    y32 = S32[:, :o.n_paths].double().cpu().numpy() / o.K - 1.0
+    S = S32[:, :o.n_paths].double().cpu().numpy()
+    y32 = S / o.K - 1.0
     y16 = Y16[:, :o.n_paths].double().cpu().numpy()
     assert np.isfinite(y16).all()
+    # both are 2^e of an FP32 exponent e (the spot, or spot over strike, folded
+    # into it) less 1 for y: each carries ln 2 times the rounding of its own e
+    # (half an FP32 ulp of e, twice: the drift and the FMA) and the rounding
+    # of 2^e; then y16 rounds once more to binary16
     u = 2.0 ** -24
-    dev = np.abs(y16 - y32) - (_ulp16(y32) + 4 * u * (1.0 + np.abs(y32)))
+    rel = np.log(2.0) * (_ulp32(np.log2(S)) + _ulp32(np.log2(S / o.K))) + 8 * u
+    dev = np.abs(y16 - y32) - (_ulp16(y32) + rel * (1.0 + np.abs(y32)))
     assert dev.max() <= 0.0, (name, np.unravel_index(dev.argmax(), dev.shape), dev.max())
     # and against the oracle's FP64 paths: the FP32 paths' 2e-5 on top
     y64 = oracle.paths(o.S0, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.seed) / o.K - 1.0

@@ -6,7 +6,7 @@ Bars:
                                        within about 1 ulp, a few ulp per
                                        bridge level)
   paths, mixed (FP32) path             rtol 2e-5: the FP32 uniform (2^-24), the
-                                       fitted quantile (<= 2.9e-7), lg2.approx
+                                       FP32 quantile (<= 2.4e-6), lg2.approx
                                        (2^-22), the FP32 bridge over <= 10
                                        levels and ex2.approx with exponent
                                        rounding (~6e-7), <~ 1e-5 worst case
@@ -157,9 +157,15 @@ PRICE_CASES = [
 # precision: the oracle's own price moves by more than 2e-4 K under path noise
 # at the FP32 paths' error level, and (volatility 150 %) under FP32 sums on
 # identical paths (tests/test_fp32_sensitivity.py).  On these two cases the
-# mixed price is held to the replay check instead (tests/lsm_replay.py: every
-# date's normal equations and the price within the FP32 bounds of the
-# kernel's own arithmetic on its own paths) and the FP64 price to 2e-4 K.
+# mixed sweep on the GPU's own paths is held to the replay check
+# (tests/lsm_replay.py: every date's normal equations and the price within the
+# FP32 bounds of the kernel's own arithmetic on its own paths).  The free-
+# running mixed price of every LSM case goes through check_mixed_vs_oracle:
+# within 2e-4 K of the oracle, or, only on an option whose oracle price itself
+# moves by more than half that under FP32-level perturbations, the replay check
+# and the FP64 price within 2e-4 K.  Besides these two, 512 dates on 3000
+# paths is such an option (its oracle price moves 2.0e-4 K under 2e-5 path
+# noise, test_many_dates_on_few_paths_are_sensitive_to_fp32_path_noise).
 UNSTABLE_IN_FP32 = {"huge_vol", "long_call"}
 
 
@@ -169,7 +175,7 @@ def test_price_vs_oracle(amc, ctx, name, opt, prec):
     ref = _oracle_price(opt)
     got = _gpu_price(amc, ctx, opt, prec)
     assert got["status"] == 0
-    if prec == 1 and name in UNSTABLE_IN_FP32 and opt.rule == 0:
+    if prec == 1 and opt.rule == 0:
         check_mixed_vs_oracle(opt, got["price"], ref["price"], lambda: _gpu_price(amc, ctx, opt, 0)["price"],
                               lambda: gpu_replay(amc, ctx, opt))
     else:
