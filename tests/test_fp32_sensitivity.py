@@ -97,3 +97,29 @@ def test_many_dates_on_few_paths_are_sensitive_to_fp32_path_noise():
     o = workloads.Option(100.0, 90.0, 0.05, 0.2, 1.0, 512, 3000, basis=3, seed=16)
     assert path_noise_spread(o) > 1e-4
     assert fp32_sum_shift(o) < 1e-5
+
+
+def test_a_365_date_put_on_8192_paths_is_unstable_at_fp32_precision():
+    """The out-of-sample tests' 365-date put (K/S0 = 1.1, sigma 40 %, T = 2,
+    8192 paths, basis 3): its oracle price moves by more than half the bar
+    under 2e-5 path noise (2.7e-4 K) and under FP32 sums (1.2e-4 K)."""
+    o = workloads.Option(100.0, 110.0, 0.02, 0.4, 2.0, 365, 8192, basis=3, seed=15)
+    assert path_noise_spread(o) > 1e-4
+    assert fp32_sum_shift(o) > 1e-4
+
+
+def test_a_served_call_below_its_european_value_is_unstable_at_fp32_precision():
+    """A request of the seed-4 serving stream: a call with S0/K = 0.98, sigma
+    25 %, T = 0.68, 281 dates, 16384 paths, basis 3, whose LSM price on the
+    oracle's points (9.026) lies below the European estimator's (9.201), the
+    early-exercise artefact of calls without dividends.  Under FP32-level
+    path noise its oracle price moves by more than half the bar (2.5e-4 K at
+    1e-6 over four draws), so check_mixed_vs_oracle holds it to the replay
+    check; two draws at 2e-5 alone had measured only 7.9e-5 K."""
+    import oracle
+    from lsm_sensitivity import fp32_noise_spread
+    o = workloads.Option(105.00634965852828, 107.03571255483877, 0.04600433471228711, 0.25053046688541913,
+                         0.6756798567826617, 281, 16384, basis=3, type=1, seed=17179871081)
+    S = oracle.paths(o.S0, o.r, o.sigma, o.T, o.n_steps, o.n_paths, o.seed)
+    assert oracle.lsm(S, o.type, o.K, o.r, o.T, o.basis)["price"] < oracle.european(S, o.type, o.K, o.r, o.T)["price"]
+    assert fp32_noise_spread(o) > 1e-4
