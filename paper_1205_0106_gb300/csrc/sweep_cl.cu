@@ -215,6 +215,21 @@ __device__ __forceinline__ float warp_sum4(const float (&v)[4], int lane) {
 // det(A_{q+1}) / (det(A_q) A_qq), leading principal minors that do not
 // depend on the diagonal scaling, decided on the high words.  Returns
 // (G^-1)_kl in lane 4k+l (k, l < p; 0 elsewhere and in lanes >= 16).
+// Totals of the 7 Gram moments over the G CTAs of the cluster from the
+// received double-float partials rm[k][c]: lane 8c'+k adds sources c',
+// c'+4, c'+8, c'+12, then a butterfly over c' (fixed order, the same in
+// every CTA); lane k (k < 7) ends with moment k, lanes 7, 15, .. with 0.
+__device__ __noinline__ dfl cl_moment_totals(const float2 (*rm)[kMaxG], int G, int lane) {
+    const int k = lane & 7, c = lane >> 3;
+    dfl acc = df_of(0.f);
+    if (k < 7)
+#pragma unroll
+        for (int s = 0; s < kMaxG; s += 4)
+            if (c + s < G) acc = df_add(acc, ld_df(rm[k][c + s]));
+    acc = df_add(acc, df_shfl_xor(acc, 8));
+    return df_add(acc, df_shfl_xor(acc, 16));
+}
+
 __device__ __noinline__ dfl cl_gram_inverse(dfl Mq, int p, int lane, bool &deg) {
     const int k = (lane >> 2) & 3, l = lane & 3;
     const dfl Mkl = df_shfl(Mq, (k + l) & 7);                 // M_{k+l} (k + l <= 6)
@@ -261,13 +276,16 @@ __device__ __noinline__ dfl cl_gram_inverse(dfl Mq, int p, int lane, bool &deg) 
     const bool in = lane < 16 && k < p && l < p;
     const dfl X = in ? df_scale(df_mul(cof, rd), Pk * Pc) : df_of(0.f);
     const dfl Gkl = in ? Mkl : df_of(0.f);
-    dfl gx = df_of(0.f);                                      // (G X)_kl = sum_q G_kq X_ql
+    // (G X)_kl = sum_q G_kq X_ql: the four products at once, then a pairwise
+    // sum (a dependent chain of 2 additions instead of 4)
+    auto matmul = [&](dfl P, dfl Q) {
+        dfl t[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) gx = df_add(gx, df_mul(df_shfl(Gkl, 4 * k + q), df_shfl(X, 4 * q + l)));
-    const dfl E = df_sub(df_of((k == l && k < p) ? 2.f : 0.f), gx);   // 2I - G X
-    dfl xn = df_of(0.f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) xn = df_add(xn, df_mul(df_shfl(X, 4 * k + q), df_shfl(E, 4 * q + l)));
+        for (int q = 0; q < 4; ++q) t[q] = df_mul(df_shfl(P, 4 * k + q), df_shfl(Q, 4 * q + l));
+        return df_add(df_add(t[0], t[1]), df_add(t[2], t[3]));
+    };
+    const dfl E = df_sub(df_of((k == l && k < p) ? 2.f : 0.f), matmul(Gkl, X));   // 2I - G X
+    const dfl xn = matmul(X, E);
     return in ? xn : df_of(0.f);
 }
 
@@ -360,12 +378,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
         if (m >= 2) {
             if (lane == 0) mbar_expect(&sm.xbarM[(m - 1) % 3], (uint32_t)(G * 7 * 8));
             ok = __all_sync(kFull, wait_bar(&sm.xbarM[(m - 1) % 3], m_parity(m - 1), true));
-            if (ok) {
-                dfl acc = df_of(0.f);
-                if (lane < 7)
-                    for (int c = 0; c < G; ++c) acc = df_add(acc, ld_df(sm.recvM[(m - 1) % 3][lane][c]));
-                ginv = cl_gram_inverse(acc, p, lane, gdeg);
-            }
+            if (ok) ginv = cl_gram_inverse(cl_moment_totals(sm.recvM[(m - 1) % 3], G, lane), p, lane, gdeg);
         }
         for (int d = m - 1; d >= 1 && ok; --d) {
             const int par = d & 1;
@@ -402,12 +415,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
             // Gram totals of date d-1 -> its inverse, off the critical path
             if (lane == 0) mbar_expect(&sm.xbarM[(d - 1) % 3], (uint32_t)(G * 7 * 8));
             ok = __all_sync(kFull, wait_bar(&sm.xbarM[(d - 1) % 3], m_parity(d - 1), true));
-            if (ok) {
-                dfl acc = df_of(0.f);
-                if (lane < 7)
-                    for (int c = 0; c < G; ++c) acc = df_add(acc, ld_df(sm.recvM[(d - 1) % 3][lane][c]));
-                ginv = cl_gram_inverse(acc, p, lane, gdeg);
-            }
+            if (ok) ginv = cl_gram_inverse(cl_moment_totals(sm.recvM[(d - 1) % 3], G, lane), p, lane, gdeg);
         }
         if (!ok) {
             bar_arrive_beta();                                // path warps waiting for a beta see the abort
