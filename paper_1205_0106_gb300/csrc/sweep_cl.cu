@@ -344,8 +344,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
     };
     // bounded wait on an mbarrier phase; the abort flag, the peers' status
     // word (a global load) and the clock are checked every 32 polls only,
-    // so that they do not delay noticing the phase
+    // so that they do not delay noticing the phase, and %globaltimer (a read
+    // of hundreds of cycles) only once the phase is found incomplete
     auto wait_bar = [&](uint64_t *b, uint32_t parity, bool peers) -> bool {
+        if (mbar_test(b, parity)) return true;
         const uint64_t t0 = globaltimer();
         for (uint32_t n = 1;; ++n) {
             if (mbar_test(b, parity)) return true;

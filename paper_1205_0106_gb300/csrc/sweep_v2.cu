@@ -231,14 +231,16 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
     if (warp < kSolvers) {
         for (int d = m - 1 - warp; d >= 1; d -= kSolvers) {
             const int b = d % 3;
-            const uint64_t t0 = globaltimer();
             bool bail = false;
-            while (sm.gtot_date[b] != d) {
-                if (sm.abort || ld_volatile_int(status) != 0 || globaltimer() - t0 > timeout_ns) {
-                    bail = true;
-                    break;
+            if (sm.gtot_date[b] != d) {
+                const uint64_t t0 = globaltimer();
+                while (sm.gtot_date[b] != d) {
+                    if (sm.abort || ld_volatile_int(status) != 0 || globaltimer() - t0 > timeout_ns) {
+                        bail = true;
+                        break;
+                    }
+                    __nanosleep(64);
                 }
-                __nanosleep(64);
             }
             bail = __any_sync(kFull, bail);
             if (bail) {
@@ -288,15 +290,20 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         bulk_load(sm.S[s], S + (int64_t)(d - 1) * ld + base, slice_bytes, &sm.mbar[s]);
         sm.pend[s] = d;
     };
+    // The bounded waits on the ring slots and the inverse read %globaltimer
+    // only once they have to wait: the read takes hundreds of cycles, and
+    // most of these waits find their condition already met.
     auto wait_slice = [&](int d) -> bool {
         const int s = d % kSlots;
         const uint32_t parity = (uint32_t)((m - d) / kSlots) & 1u;
-        const uint64_t t0 = globaltimer();
-        while (!mbar_test(&sm.mbar[s], parity)) {
-            if (sm.abort || globaltimer() - t0 > timeout_ns) {
-                atomicCAS(status, 0, AMC_ETIMEOUT);
-                sm.abort = 1;
-                return false;
+        if (!mbar_test(&sm.mbar[s], parity)) {
+            const uint64_t t0 = globaltimer();
+            while (!mbar_test(&sm.mbar[s], parity)) {
+                if (sm.abort || globaltimer() - t0 > timeout_ns) {
+                    atomicCAS(status, 0, AMC_ETIMEOUT);
+                    sm.abort = 1;
+                    return false;
+                }
             }
         }
         if (w == 0) sm.pend[s] = 0;
@@ -498,6 +505,8 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             const uint32_t tag = tag_hi | (uint32_t)jx;
             uint64_t *xg = xch + ((size_t)jx * kXV + xk) * G;
             float vals[kMaxCtas / 32];
+            // the clock is read before the first poll: its latency also delays
+            // that poll, and polling earlier only adds loaded L2 round trips
             const uint64_t t0 = globaltimer();
             for (;;) {
                 bool good = true;
@@ -544,12 +553,14 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             // beta_j = Ginv_j R_j in double-float, in every path warp: lane
             // 4k+l one product, two butterfly steps, then beta_k from lane 4k
             const int b = j % 3;
-            const uint64_t t0 = globaltimer();
             bool bail = false;
-            while (sm.ginv_date[b] != j) {
-                if (sm.abort || globaltimer() - t0 > timeout_ns) {
-                    bail = true;
-                    break;
+            if (sm.ginv_date[b] != j) {
+                const uint64_t t0 = globaltimer();
+                while (sm.ginv_date[b] != j) {
+                    if (sm.abort || globaltimer() - t0 > timeout_ns) {
+                        bail = true;
+                        break;
+                    }
                 }
             }
             if (__any_sync(kFull, bail)) {
