@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
             bool stop = !wait_bar(&sm.mbar[m % kSlots], slot_parity(m), false);
             if (!stop) {
                 const E *sl = sm.S[m % kSlots];
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < kPPT; ++i) {
                     const int idx = pidx(i);
                     const float y = raw_y(sl, idx, invK);
@@ -497,12 +497,12 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 constexpr int kFullRounds = kPairs / kPathThreads;           // 8
                 auto all_pairs = [&](auto P4) {
                     if (nloc == kPPC) {
-    #pragma unroll
+#pragma unroll
                         for (int s2 = 0; s2 < kFullRounds; ++s2) pair(2 * (t + kPathThreads * s2), false, P4);
                         if (t + kPathThreads * kFullRounds < kPairs)
                             pair(2 * (t + kPathThreads * kFullRounds), false, P4);
                     } else {
-    #pragma unroll 2
+#pragma unroll 2
                         for (int q = t; q < kPairs; q += kPathThreads) pair(2 * q, true, P4);
                     }
                 };
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                     // P4: the cubic basis; otherwise b3 = 0 and R3 is not used (p <= 3)
                     auto ex_rhs = [&](auto P4) {
                         constexpr bool Q4 = decltype(P4)::value;
-    #pragma unroll
+#pragma unroll
                     for (int i = 0; i < kPPT; i += 2) {
                         const int idx = pidx(i);
                         if (ex) {
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 } else if (!sm.deg[1]) {
                     const float b0 = sm.beta[1][0], b1 = sm.beta[1][1], b2 = sm.beta[1][2], b3 = sm.beta[1][3];
                     const E *se = sm.S[1 % kSlots];
-    #pragma unroll
+#pragma unroll
                     for (int i = 0; i < kPPT; ++i) {
                         const float y = y_at(se, pidx(i));
                         const float cont = fmaf(fmaf(fmaf(b3, y, b2), y, b1), y, b0);
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
             // final per-thread sums (units of K): CF, CF^2
             float fs[4] = {0.f, 0.f, 0.f, 0.f};
             if (!stop) {
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < kPPT; ++i) {
                     if (pidx(i) >= nloc) continue;
                     fs[0] += cf[i];
