@@ -143,6 +143,15 @@ __device__ __forceinline__ uint32_t map_to(uint32_t local, uint32_t rank) {
 }
 // One double-float partial into CTA `rank`'s receive slot, counted on its
 // exchange mbarrier (8 bytes of transaction).
+// FP32 butterfly sum of one value per lane, the same in every lane: a CTA's
+// total of the path warps' partials before it is sent (on the path warps'
+// critical path, where a double-float butterfly took about 300 cycles more;
+// the CTAs' totals are then added in double-float)
+__device__ __forceinline__ float f_warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
 __device__ __forceinline__ void send_df(uint32_t dst, uint32_t bar, float hi, float lo) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(dst),
                  "f"(hi), "f"(lo), "r"(bar)
@@ -519,7 +528,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
             auto send_gram = [&](int e) {    // after the path-warp barrier that completes redM[e & 1]
                 const int v = warp - 5;
                 if (v >= 0 && v < 7) {
-                    const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redM[e & 1][lane][v] : 0.f));
+                    const dfl tot = df_of(f_warp_sum(lane < kPathWarps ? sm.redM[e & 1][lane][v] : 0.f));
                     if (lane < G && inject_date != e + 1) {
                         send_df(map_to(saddr(&sm.recvM[e % 3][v][lc]), (uint32_t)lane),
                                 map_to(saddr(&sm.xbarM[e % 3]), (uint32_t)lane), tot.hi, tot.lo);
@@ -608,7 +617,7 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                 {
                     const int v = warp - 1;                               // warps 1..4: right-hand side v
                     if (v < 4) {
-                        const dfl tot = df_warp_sum(df_of(lane < kPathWarps ? sm.redR[par][lane][v] : 0.f));
+                        const dfl tot = df_of(f_warp_sum(lane < kPathWarps ? sm.redR[par][lane][v] : 0.f));
                         if (lane < G && inject_date != d) {
                             send_df(map_to(saddr(&sm.recvR[par][v][lc]), (uint32_t)lane),
                                     map_to(saddr(&sm.xbarR[par]), (uint32_t)lane), tot.hi, tot.lo);

@@ -29,10 +29,12 @@ u = 2^-24, where
               of |y|^k Cmax
             + sum over ambiguous in-the-money paths of |y|^k (|CF| + Cmax).
 The terms:
-  24u      per sum: up to 7 FP32 additions per thread (8 paths), 5 levels of
-           the warp tree, the FP32 rounding of each CTA's double-float partial
-           (the CTAs' and warps' partials are added in double-float), and up
-           to 3 roundings in forming a term y^q or y^k CF; 24u > 18u;
+  24u      per sum: a term y^q or y^k CF is formed with up to 3 roundings,
+           then passes through at most 10 FP32 additions in its thread (the
+           cluster sweep's 8 or 9 packed pairs and the pair's two halves, or
+           its one shared-memory path; 8 paths in the L2-exchange sweep), 5
+           levels of the warp tree and 5 of the FP32 tree over the CTA's
+           warps; the CTAs' totals are added in double-float; 23u < 24u;
   dy       the GPU forms y = fma(S, fl(1/K), -1) in FP32:
            |dy| <= u (1 + 2|y|);
   dCF      the GPU's cash flow is h (from its y) discounted by fl(e^{-r dt})
