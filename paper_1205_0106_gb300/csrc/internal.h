@@ -118,7 +118,7 @@ constexpr uint32_t kEpochBits = 22; // tag = epoch << 10 | exchange index
 inline int v2_ctas(int64_t n_paths) { return (int)((n_paths + kV2PathsPerCta - 1) / kV2PathsPerCta); }
 inline size_t v2_xch_units(int m, int ctas) { return (size_t)(m + 2) * kXV * ctas; }
 constexpr int kPathgenThreads = 128;
-constexpr int kPathgenQ = 4;        // points per thread per tile (strided by 128)
+constexpr int kPathgenQ = 4;        // consecutive points per thread per tile
 constexpr int kTilePoints = kPathgenThreads * kPathgenQ;
 
 // Kernel arguments, passed by value (__grid_constant__): either a device
