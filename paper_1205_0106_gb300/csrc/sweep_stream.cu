@@ -287,7 +287,7 @@ __device__ __forceinline__ double to_d(double x) { return x; }
 // final pass (exercise of date 1, sums of CF).  H16: the path array holds
 // binary16 moneyness (12 instead of 16 bytes per path and date).
 template <bool FP64, bool PUT, bool H16>
-__global__ void __launch_bounds__(kStreamThreads) lsm_stream_pass(const __grid_constant__ StreamArgs a, int j) {
+__global__ void __launch_bounds__(kStreamThreads, (FP64 || H16) ? 3 : 4) lsm_stream_pass(const __grid_constant__ StreamArgs a, int j) {
     static_assert(!(FP64 && H16), "binary16 moneyness is an FP32-path format");
     using Real = typename ST<FP64>::Real;
     using Elem = typename std::conditional<H16, uint16_t, Real>::type;
