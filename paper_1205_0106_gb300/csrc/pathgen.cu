@@ -60,7 +60,7 @@ struct alignas(4 * sizeof(Real)) R4 {
 // factors applied (the same products the node loop would form).
 template <typename Real>
 struct alignas(16) NodeX {
-    int32_t v4;                   // first of the dimension's 3 uint4 of direction numbers
+    int32_t v4;                   // first of the dimension's 2 uint4 of direction numbers v_1..v_8
     int32_t coord;                // Sobol' dimension
     int32_t wl_o, wr_o, wo_o;     // byte offsets of the left, right and own stack slots
     int32_t date;
@@ -74,7 +74,7 @@ struct alignas(16) NodeX {
 // coefficients and a flag per date); one that takes the paper's rule holds
 // two discounted-payoff constants per date.
 struct PathgenSmem {
-    unsigned nodes, v, xb, W, coef, deg, total;
+    unsigned nodes, v, v9, xb, W, coef, deg, total;
 };
 __host__ __device__ __forceinline__ unsigned al32(unsigned v) { return (v + 31u) & ~31u; }
 __host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int nslots, bool fp64, int mode = 0) {
@@ -86,7 +86,8 @@ __host__ __device__ __forceinline__ PathgenSmem pathgen_layout(int max_m, int ns
     const unsigned real = fp64 ? 8u : 4u;
     L.nodes = 0;
     L.v = al32(L.nodes + node * (unsigned)max_m);
-    L.xb = al32(L.v + 48u * (unsigned)max_m);
+    L.v9 = al32(L.v + 32u * (unsigned)max_m);             // v_1..v_8 as two uint4 per dimension, then v_9
+    L.xb = al32(L.v9 + 4u * (unsigned)max_m);
     L.W = al32(L.xb + 4u * (unsigned)max_m);
     L.coef = al32(L.W + real * 4u * kPathgenThreads * (unsigned)nslots);
     L.deg = al32(L.coef + real * per_date * (unsigned)max_m);
@@ -169,7 +170,7 @@ __device__ __forceinline__ void node_points(const uint32_t (&xq)[4], Real wl, Re
 
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 constexpr int kGB = ilog2(kTilePoints) - 1;       // Gray bits 1..kGB of the thread's point offset 4t
-static_assert((1 << ilog2(kTilePoints)) == kTilePoints && kGB + 1 < 12, "tile of 2^k points, direction numbers v_1..v_12");
+static_assert((1 << ilog2(kTilePoints)) == kTilePoints && kGB + 1 <= 9, "tile of 2^k points, direction numbers v_1..v_9");
 
 // MODE kStore writes the path array (steps 1-3); kStore16 writes it as
 // binary16 moneyness y = S/K - 1 (8 bytes per thread and date).  The other
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     Real(*s_ab)[2] = reinterpret_cast<Real(*)[2]>(smem + L.coef);            // [m][2] paper rule: a_d, b_d
     unsigned char *s_deg = smem + L.deg;                                    // [m] no exercise at the date
     NodeX<Real> *s_nodes = reinterpret_cast<NodeX<Real> *>(smem + L.nodes);
-    uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][3]: v_1..v_12 of each dim
+    uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][2]: v_1..v_8 of each dim
+    uint32_t *s_v9 = reinterpret_cast<uint32_t *>(smem + L.v9);            // [m]: v_9 of each dim
     uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift
     R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);              // [slot][128]
 
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             for (int i = tid; i < m; i += kPathgenThreads) {
                 const Node g = gn[i];
                 NodeX<Real> x;
-                x.v4 = 3 * g.coord;
+                x.v4 = 2 * g.coord;
                 x.coord = g.coord;
                 x.wl_o = g.sl * kSlotBytes;
                 x.wr_o = g.sr * kSlotBytes;
@@ -252,8 +254,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
                 x.row = (int64_t)(g.date - 1) * J.ld;
                 s_nodes[i] = x;
             }
-            for (int i = tid; i < 3 * m; i += kPathgenThreads)
-                s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 3) * 32) + (i % 3));
+            for (int i = tid; i < 2 * m; i += kPathgenThreads)
+                s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 2) * 32) + (i % 2));
+            for (int i = tid; i < m; i += kPathgenThreads) s_v9[i] = __ldg(V + i * 32 + 8);
             if (MODE == kPaperRule) {
                 // e^{-r t_d} h(S) = a_d + b_d S where h > 0 (put: a_d = e^{-r t_d} K, b_d = -e^{-r t_d})
                 for (int d = tid; d < m; d += kPathgenThreads) {
@@ -316,8 +319,8 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
 #pragma unroll ((!FP64 && (STORE || MODE == kPaperRule)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
             const NodeX<Real> nd = s_nodes[n];
-            const uint4 v0 = s_v[nd.v4], v1 = s_v[nd.v4 + 1], v2 = s_v[nd.v4 + 2];
-            const uint32_t vd[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+            const uint4 v0 = s_v[nd.v4], v1 = s_v[nd.v4 + 1];
+            const uint32_t vd[9] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, s_v9[nd.coord]};
             uint32_t x0 = s_xb[nd.coord];
 #pragma unroll
             for (int b = 0; b < kGB; ++b) x0 ^= vd[b + 1] & gm[b];
