@@ -21,7 +21,7 @@ import pytest
 import oracle
 import workloads
 from lsm_replay import gpu_fit, gpu_replay, replay_check
-from lsm_sensitivity import check_mixed_vs_oracle
+from lsm_sensitivity import check_mixed_vs_oracle, fp32_sum_shift
 
 pytestmark = pytest.mark.gpu
 
@@ -165,7 +165,12 @@ PRICE_CASES = [
 # moves by more than half that under FP32-level perturbations, the replay check
 # and the FP64 price within 2e-4 K.  Besides these two, 512 dates on 3000
 # paths is such an option (its oracle price moves 2.0e-4 K under 2e-5 path
-# noise, test_many_dates_on_few_paths_are_sensitive_to_fp32_path_noise).
+# noise, test_many_dates_on_few_paths_are_sensitive_to_fp32_path_noise), and
+# so is the 365-date put on 8192 paths, whose oracle price moves 1.2e-4 K
+# under FP32 sums on identical paths alone
+# (test_a_365_date_put_on_8192_paths_is_unstable_at_fp32_precision): the
+# mixed sweep on identical paths may miss the bar there, by its summation
+# order, and is then held to the replay check alone.
 UNSTABLE_IN_FP32 = {"huge_vol", "long_call"}
 
 
@@ -197,8 +202,10 @@ def test_mixed_sweep_on_identical_paths(amc, ctx, torch, name, opt):
         d = replay_check(Sh, opt, coef, got)
         assert d["residual_ratio"] <= 1.0
         ref = oracle.lsm(Sh, opt.type, opt.K, opt.r, opt.T, opt.basis)
-        if name not in UNSTABLE_IN_FP32:
-            assert abs(got["price"] - ref["price"]) <= 2e-4 * opt.K, (got, ref)
+        if name not in UNSTABLE_IN_FP32 and abs(got["price"] - ref["price"]) > 2e-4 * opt.K:
+            # a miss is allowed only where FP32 sums alone, on identical
+            # paths, move the oracle's own price by more than half the bar
+            assert fp32_sum_shift(opt) > 1e-4, (got, ref)
         assert got["degenerate_dates"] == ref["degenerate_dates"]
         return
     ld = amc.amc_path_ld(opt.n_paths)
