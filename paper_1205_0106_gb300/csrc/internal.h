@@ -13,8 +13,9 @@ namespace amc {
 // Brownian-bridge node, in the depth-first evaluation order used by the
 // path-generation kernel.  `coord` is the Sobol' dimension that the
 // breadth-first numbering gives this node; `sl`/`sr`/`so` are slots of the
-// per-path stack (slot d holds the latest node of depth d; slot `zero_slot`
-// holds W(0) = 0).  W(t_date) = wl W(t_l) + wr W(t_r) + sdu sqrt(dt) z.
+// per-path stack (slot d holds the latest node of depth d).
+// W(t_date) = wl W(t_l) + wr W(t_r) + sdu sqrt(dt) z; a node with t_l = 0
+// has wl = 0 and sl = sr (W(0) = 0 has no slot), the root wl = wr = 0.
 struct NodeF {
     int32_t coord, date;
     int16_t sl, sr, so, pad;
@@ -28,11 +29,11 @@ struct NodeD {
 static_assert(sizeof(NodeF) == 32, "NodeF layout");
 static_assert(sizeof(NodeD) == 40, "NodeD layout");
 
-constexpr int kMaxSlots = 12;       // depth <= 10 for m <= 512, plus the zero slot
+constexpr int kMaxSlots = 12;       // depth <= 10 for m <= 512: 11 slots
 
 struct BridgePlan {
     int m = 0;
-    int nslots = 0;                 // stack slots including the zero slot
+    int nslots = 0;                 // stack slots (the tree's depth + 1)
     std::vector<NodeF> nf;          // depth-first order
     std::vector<NodeD> nd;
 };

@@ -57,16 +57,19 @@ struct alignas(4 * sizeof(Real)) R4 {
 
 // A bridge node as pathgen_kernel reads it, expanded from NodeF/NodeD once
 // per job: shared-memory offsets instead of indices, and the job's scale
-// factors applied (the same products the node loop would form).
+// factors applied (the same products the node loop would form).  32 bytes
+// in FP32; the node's direction numbers and tile integers sit in tables
+// indexed by node, so the record holds no Sobol' dimension.
 template <typename Real>
 struct alignas(16) NodeX {
-    int32_t v4;                   // first of the dimension's 2 uint4 of direction numbers v_1..v_8
-    int32_t coord;                // Sobol' dimension
-    int32_t wl_o, wr_o, wo_o;     // byte offsets of the left, right and own stack slots
-    int32_t date;
+    uint16_t wl_o, wr_o, wo_o;    // byte offsets of the left, right and own stack slots
+    uint16_t date;
     Real wl, wr, sd, drift;       // bridge weights, sdu sqrt(dt), the exponent's constant (node_points)
     int64_t row;                  // (date - 1) ld: element offset of the date's row
 };
+static_assert(sizeof(NodeX<float>) == 32 && sizeof(NodeX<double>) == 48, "node records");
+static_assert(kMaxSlots * kPathgenThreads * sizeof(double) * 4 <= 65536 && AMC_MAX_STEPS < 65536,
+              "slot offsets and dates fit 16 bits");
 
 // Shared-memory layout of the path-generation kernel: every sub-buffer
 // starts on a 32-byte boundary (uint4 and R4<double> accesses).  A kernel
@@ -203,9 +206,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     Real(*s_ab)[2] = reinterpret_cast<Real(*)[2]>(smem + L.coef);            // [m][2] paper rule: a_d, b_d
     unsigned char *s_deg = smem + L.deg;                                    // [m] no exercise at the date
     NodeX<Real> *s_nodes = reinterpret_cast<NodeX<Real> *>(smem + L.nodes);
-    uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][2]: v_1..v_8 of each dim
-    uint32_t *s_v9 = reinterpret_cast<uint32_t *>(smem + L.v9);            // [m]: v_9 of each dim
-    uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift
+    uint4 *s_v = reinterpret_cast<uint4 *>(smem + L.v);                    // [m][2]: v_1..v_8 of each node's dim
+    uint32_t *s_v9 = reinterpret_cast<uint32_t *>(smem + L.v9);            // [m]: v_9 of each node's dim
+    uint32_t *s_xb = reinterpret_cast<uint32_t *>(smem + L.xb);            // [m]: x(tile) xor shift, by node
     R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);              // [slot][128]
 
     const uint32_t *__restrict__ V = a.V;
@@ -218,8 +221,18 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
     // FP32: the integers' top bit flipped once here (x - 2^31 as signed values, node_points)
     const uint32_t flip = FP64 ? 0u : 0x80000000u;
     unsigned char *const Wt = reinterpret_cast<unsigned char *>(s_W + tid);   // this thread's slot 0
+    {
+        // every stack slot starts at 0: the root, and a node whose left end
+        // point is W(0) = 0, read a slot with weight 0 (never before it is
+        // written in that tile but for these reads), which must hold a
+        // finite value
+        R4<Real> zero;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
+        for (int sl = 0; sl < a.max_slots; ++sl) s_W[sl * kPathgenThreads + tid] = zero;
+    }
     int cur = -1;
-    int m = 0, nslots = 0;
+    int m = 0;
     double vs1 = 0.0, vs2 = 0.0;                                          // this thread's path values (fused modes)
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
         const int jb = a.jobs ? find_job_by_tile(a.jobs, a.n_jobs, tile) : 0;
@@ -229,7 +242,6 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
         __syncthreads();                                                  // previous tile done with smem
         if (jb != cur) {
             m = J.m;
-            nslots = J.nslots;
             const Node *gn = reinterpret_cast<const Node *>(J.nodes);
             const double mu = J.r - 0.5 * J.sigma * J.sigma;
             const Real sqdt = (Real)sqrt(J.dt);
@@ -241,22 +253,21 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             for (int i = tid; i < m; i += kPathgenThreads) {
                 const Node g = gn[i];
                 NodeX<Real> x;
-                x.v4 = 2 * g.coord;
-                x.coord = g.coord;
-                x.wl_o = g.sl * kSlotBytes;
-                x.wr_o = g.sr * kSlotBytes;
-                x.wo_o = g.so * kSlotBytes;
-                x.date = g.date;
+                x.wl_o = (uint16_t)(g.sl * kSlotBytes);
+                x.wr_o = (uint16_t)(g.sr * kSlotBytes);
+                x.wo_o = (uint16_t)(g.so * kSlotBytes);
+                x.date = (uint16_t)g.date;
                 x.wl = (Real)g.wl;
                 x.wr = (Real)g.wr;
                 x.sd = (Real)g.sdu * sqdt;
                 x.drift = FP64 ? mu_dt * (Real)g.date : (Real)(mu_dt2 * (double)g.date + lS0);
                 x.row = (int64_t)(g.date - 1) * J.ld;
                 s_nodes[i] = x;
+                const uint4 *Vd = reinterpret_cast<const uint4 *>(V + g.coord * 32);
+                s_v[2 * i] = __ldg(Vd);
+                s_v[2 * i + 1] = __ldg(Vd + 1);
+                s_v9[i] = __ldg(V + g.coord * 32 + 8);
             }
-            for (int i = tid; i < 2 * m; i += kPathgenThreads)
-                s_v[i] = __ldg(reinterpret_cast<const uint4 *>(V + (i / 2) * 32) + (i % 2));
-            for (int i = tid; i < m; i += kPathgenThreads) s_v9[i] = __ldg(V + i * 32 + 8);
             if (MODE == kPaperRule) {
                 // e^{-r t_d} h(S) = a_d + b_d S where h > 0 (put: a_d = e^{-r t_d} K, b_d = -e^{-r t_d})
                 for (int d = tid; d < m; d += kPathgenThreads) {
@@ -276,12 +287,12 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
             }
             cur = jb;
         }
-        for (int k = tid; k < m; k += kPathgenThreads) s_xb[k] = sobol_direct(V, k, base) ^ shift[k] ^ flip;
         {
-            R4<Real> zero;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
-            s_W[(nslots - 1) * kPathgenThreads + tid] = zero;
+            const Node *gn = reinterpret_cast<const Node *>(J.nodes);
+            for (int k = tid; k < m; k += kPathgenThreads) {
+                const int c = __ldg(&gn[k].coord);
+                s_xb[k] = sobol_direct(V, c, base) ^ shift[c] ^ flip;
+            }
         }
         __syncthreads();
 
@@ -319,9 +330,9 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_kernel(const __grid_c
 #pragma unroll ((!FP64 && (STORE || MODE == kPaperRule)) ? 8 : 1)
         for (int n = 0; n < m; ++n) {
             const NodeX<Real> nd = s_nodes[n];
-            const uint4 v0 = s_v[nd.v4], v1 = s_v[nd.v4 + 1];
-            const uint32_t vd[9] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, s_v9[nd.coord]};
-            uint32_t x0 = s_xb[nd.coord];
+            const uint4 v0 = s_v[2 * n], v1 = s_v[2 * n + 1];
+            const uint32_t vd[9] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, s_v9[n]};
+            uint32_t x0 = s_xb[n];
 #pragma unroll
             for (int b = 0; b < kGB; ++b) x0 ^= vd[b + 1] & gm[b];
             const uint32_t xq[4] = {x0, x0 ^ v0.x, x0 ^ v0.x ^ v0.y, x0 ^ v0.y};
@@ -450,7 +461,7 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
     using Node = typename PG<FP64>::Node;
     extern __shared__ __align__(32) unsigned char smem[];
     const Job &J = a.one;
-    const int m = J.m, nslots = J.nslots;
+    const int m = J.m;
     const PathgenSmem L = pathgen_layout(m, a.max_slots, FP64);
     Node *s_nodes = reinterpret_cast<Node *>(smem + L.nodes);
     R4<Real> *s_W = reinterpret_cast<R4<Real> *>(smem + L.W);
@@ -467,16 +478,16 @@ __global__ void __launch_bounds__(kPathgenThreads) pathgen_perm_kernel(const __g
     const Real mu_dt = (Real)(mu * J.dt);                                  // FP64
     const double mu_dt2 = mu * J.dt * 1.4426950408889634, lS0 = log2(J.S0);   // FP32: base 2, spot folded in
     const Real sig = FP64 ? (Real)J.sigma : (Real)(J.sigma * 1.4426950408889634);
+    {
+        // every stack slot starts at 0 (the reads with weight 0, pathgen_kernel)
+        R4<Real> zero;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
+        for (int sl = 0; sl < a.max_slots; ++sl) s_W[sl * kPathgenThreads + tid] = zero;
+    }
     for (int64_t tile = blockIdx.x; tile < a.total; tile += gridDim.x) {
         const uint64_t base = (uint64_t)tile * kTilePoints;
         __syncthreads();                                                  // previous tile done with smem
-        {
-            R4<Real> zero;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) zero.v[q] = Real(0);
-            s_W[(nslots - 1) * kPathgenThreads + tid] = zero;
-        }
-        __syncthreads();
         const bool store = (int64_t)(base + 4u * tid) < ld;
         Real *__restrict__ S = reinterpret_cast<Real *>(J.S) + base + 4u * tid;
         for (int n = 0; n < m; ++n) {

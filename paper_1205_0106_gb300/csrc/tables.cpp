@@ -106,8 +106,12 @@ int host_bridge_bfs(int m, int32_t *date, int32_t *left, int32_t *right) {
 
 // Depth-first evaluation plan of the same bridge.  A node only needs the W
 // of its interval end points, which are its ancestors; with one stack slot
-// per tree depth those are always resident, so a path needs depth+2 slots
-// instead of m values of shared memory.
+// per tree depth those are always resident, so a path needs depth+1 slots
+// instead of m values of shared memory.  W(0) = 0 needs none: a node on
+// [0, r] has no left term (wl = 0, and it reads its right end point's slot
+// in place of a left one), and the root has no terms at all (wl = wr = 0,
+// reading its own slot); the kernels start every slot at 0, so these reads
+// with weight 0 always meet finite values.
 int host_bridge_plan(int m, BridgePlan *plan) {
     std::vector<int32_t> date(m), left(m), right(m);
     int rc = host_bridge_bfs(m, date.data(), left.data(), right.data());
@@ -118,19 +122,19 @@ int host_bridge_plan(int m, BridgePlan *plan) {
     plan->nf.clear();
     plan->nd.clear();
     int maxdepth = 0;
-    auto emit = [&](int d, int l, int r, int depth, int zero_slot) {
+    auto emit = [&](int d, int l, int r, int depth) {
         NodeD n{};
         n.coord = coord_of_date[d];
         n.date = d;
         n.so = (int16_t)depth;
         if (depth == 0) {                               // W(t_m) = sqrt(t_m) z_0
-            n.sl = n.sr = (int16_t)zero_slot;
+            n.sl = n.sr = 0;
             n.wl = n.wr = 0.0;
             n.sdu = sqrt((double)m);
-        } else {
-            n.sl = (int16_t)(l == 0 ? zero_slot : slot_of_date[l]);
-            n.sr = (int16_t)(r == 0 ? zero_slot : slot_of_date[r]);
-            n.wl = (double)(r - d) / (double)(r - l);
+        } else {                                        // r >= 1: an earlier node's date
+            n.sr = (int16_t)slot_of_date[r];
+            n.sl = (int16_t)(l == 0 ? n.sr : slot_of_date[l]);
+            n.wl = l == 0 ? 0.0 : (double)(r - d) / (double)(r - l);   // W(0) = 0: no left term
             n.wr = (double)(d - l) / (double)(r - l);
             n.sdu = sqrt((double)(d - l) * (double)(r - d) / (double)(r - l));
         }
@@ -150,10 +154,9 @@ int host_bridge_plan(int m, BridgePlan *plan) {
         st.push_back({{mid, r}, e.second + 1});
         st.push_back({{l, mid}, e.second + 1});
     }
-    const int zero_slot = maxdepth + 1;
-    plan->nslots = zero_slot + 1;
+    plan->nslots = maxdepth + 1;
     if (plan->nslots > kMaxSlots) return AMC_EINVAL;
-    emit(m, 0, 0, 0, zero_slot);
+    emit(m, 0, 0, 0);
     // second pass: depth-first, left subtree first
     st.push_back({{0, m}, 1});
     while (!st.empty()) {
@@ -162,7 +165,7 @@ int host_bridge_plan(int m, BridgePlan *plan) {
         int l = e.first.first, r = e.first.second;
         if (r - l < 2) continue;
         int mid = (l + r) / 2;
-        emit(mid, l, r, e.second, zero_slot);
+        emit(mid, l, r, e.second);
         st.push_back({{mid, r}, e.second + 1});
         st.push_back({{l, mid}, e.second + 1});
     }
