@@ -175,6 +175,16 @@ int amc_sobol_directions(int n_dims, uint32_t *out);
 /* Bridge schedule in coordinate order k = 0..m-1: the date filled by
  * coordinate k and the dates it is conditioned on (0 = W(0) = 0).          */
 int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *right);
+/* The same bridge (ref. [13]; §III.D) in the depth-first order that path
+ * generation evaluates it (inspection path; each array holds n_steps
+ * entries): node k forms W(t_date[k]) = wl[k] W[sl[k]] + wr[k] W[sr[k]] +
+ * sdu[k] sqrt(T / n_steps) z_coord[k] from the per-path stack W[0..n_slots-1],
+ * which starts at 0, and stores it in W[so[k]].  W(0) = 0 takes no slot: a
+ * node on [0, t_r] has wl = 0 and reads its right end point twice, and the
+ * first node (t_m) has wl = wr = 0.  AMC_EINVAL for n_steps outside
+ * 1..AMC_MAX_STEPS or a null pointer.                                      */
+int amc_bridge_plan(int n_steps, int32_t *coord, int32_t *date, int32_t *sl, int32_t *sr, int32_t *so, double *wl,
+                    double *wr, double *sdu, int32_t *n_slots);
 /* CTAs the sweep gives one option of n_paths paths in precision `prec`
  * under `rule` (a pure function of these and the device's SM count), and
  * the paths each sweep thread owns.  AMC_EINVAL when the option's per-path

@@ -87,6 +87,7 @@ SIGNATURES = {
     "amc_digital_shifts": (ctypes.c_int, [_u64, ctypes.c_int, _u32p]),
     "amc_sobol_directions": (ctypes.c_int, [ctypes.c_int, _u32p]),
     "amc_bridge_schedule": (ctypes.c_int, [ctypes.c_int, _i32p, _i32p, _i32p]),
+    "amc_bridge_plan": (ctypes.c_int, [ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _dp, _dp, _dp, _i32p]),
     "amc_plan_sweep": (ctypes.c_int, [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p]),
     "amc_sobol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, _u64, _vp, _i64, _vp]),
     "amc_generate_paths": (ctypes.c_int, [_vp, _optp, ctypes.c_int, _vp, _i64, _vp]),
@@ -212,6 +213,20 @@ def amc_bridge_schedule(n_steps):
     _check(lib().amc_bridge_schedule(n_steps, d.ctypes.data_as(_i32p), l.ctypes.data_as(_i32p),
                                      r.ctypes.data_as(_i32p)), "amc_bridge_schedule")
     return d, l, r
+
+
+def amc_bridge_plan(n_steps):
+    """The depth-first evaluation plan of the bridge: a dict of per-node arrays
+    (coord, date, sl, sr, so, wl, wr, sdu) and the slot count n_slots."""
+    import numpy as np
+    n = max(1, min(n_steps, AMC_MAX_STEPS))             # the library rejects n_steps outside 1..AMC_MAX_STEPS
+    ints = {k: np.zeros(n, dtype=np.int32) for k in ("coord", "date", "sl", "sr", "so")}
+    dbls = {k: np.zeros(n, dtype=np.float64) for k in ("wl", "wr", "sdu")}
+    ns = ctypes.c_int32()
+    _check(lib().amc_bridge_plan(n_steps, *(ints[k].ctypes.data_as(_i32p) for k in ("coord", "date", "sl", "sr", "so")),
+                                 *(dbls[k].ctypes.data_as(_dp) for k in ("wl", "wr", "sdu")), ctypes.byref(ns)),
+           "amc_bridge_plan")
+    return dict(**ints, **dbls, n_slots=ns.value)
 
 
 def amc_plan_sweep(n_paths, sm_count, prec=AMC_MIXED, rule=AMC_RULE_LSM):

@@ -794,6 +794,26 @@ int amc_bridge_schedule(int n_steps, int32_t *date, int32_t *left, int32_t *righ
     if (!date || !left || !right) return AMC_EINVAL;
     return host_bridge_bfs(n_steps, date, left, right);
 }
+int amc_bridge_plan(int n_steps, int32_t *coord, int32_t *date, int32_t *sl, int32_t *sr, int32_t *so, double *wl,
+                    double *wr, double *sdu, int32_t *n_slots) {
+    if (!coord || !date || !sl || !sr || !so || !wl || !wr || !sdu || !n_slots) return AMC_EINVAL;
+    if (n_steps < 1 || n_steps > AMC_MAX_STEPS) return AMC_EINVAL;
+    BridgePlan plan;
+    AMC_TRY(host_bridge_plan(n_steps, &plan));
+    for (int k = 0; k < n_steps; ++k) {
+        const NodeD &n = plan.nd[k];
+        coord[k] = n.coord;
+        date[k] = n.date;
+        sl[k] = n.sl;
+        sr[k] = n.sr;
+        so[k] = n.so;
+        wl[k] = n.wl;
+        wr[k] = n.wr;
+        sdu[k] = n.sdu;
+    }
+    *n_slots = plan.nslots;
+    return AMC_OK;
+}
 int amc_plan_sweep(int64_t n_paths, int sm_count, int prec, int rule, int32_t *ctas, int32_t *paths_per_thread) {
     SweepPlan p;
     int rc = host_plan_sweep(n_paths, sm_count, prec, rule, &p);

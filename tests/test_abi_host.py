@@ -76,6 +76,38 @@ def test_library_bridge_schedule(amc, m):
         assert d.tolist() == [16, 8, 4, 12, 2, 6, 10, 14, 1, 3, 5, 7, 9, 11, 13, 15]
 
 
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 7, 16, 50, 252, 365, 512])
+def test_bridge_plan_evaluates_the_bridge_matrix(amc, m):
+    """The depth-first plan the path-generation kernels run, evaluated here
+    with its slot stack in FP64, gives W = A z with the oracle's bridge matrix
+    A (pinned to A A^T = min(t_i, t_j)).  The stack starts at a finite value
+    other than 0 as well: the result does not change, so every read of a slot
+    not yet written in the pass (W(0) has no slot) carries weight 0."""
+    import oracle
+    p = amc.amc_bridge_plan(m)
+    assert sorted(p["date"].tolist()) == list(range(1, m + 1)) and p["date"][0] == m
+    assert sorted(p["coord"].tolist()) == list(range(m))
+    assert 1 <= p["n_slots"] <= 11 and p["so"].max() < p["n_slots"]
+    T = 1.3
+    A = oracle.bridge_matrix(m, T)
+    Z = np.random.default_rng(m).standard_normal((m, 3))
+    for start in (0.0, 7.25):
+        st = np.full((p["n_slots"], 3), start)
+        W = np.zeros((m, 3))
+        for k in range(m):
+            w = p["wl"][k] * st[p["sl"][k]] + p["wr"][k] * st[p["sr"][k]] + p["sdu"][k] * np.sqrt(T / m) * Z[p["coord"][k]]
+            st[p["so"][k]] = w
+            W[p["date"][k] - 1] = w
+        np.testing.assert_allclose(W, A @ Z, rtol=1e-12, atol=1e-12)
+
+
+def test_bridge_plan_rejects_bad_sizes(amc):
+    for m in (0, -1, amc.AMC_MAX_STEPS + 1):
+        with pytest.raises(amc.AmcError) as ei:
+            amc.amc_bridge_plan(m)
+        assert ei.value.code == amc.AMC_EINVAL
+
+
 def test_validation(amc):
     import workloads
     good = workloads.single_small()
