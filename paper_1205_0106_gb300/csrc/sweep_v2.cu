@@ -315,35 +315,43 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
         // the in-the-money indicator I = sat(-y 2^100) (put) or sat(y 2^100)
         // (call) is exactly 1 for a nonzero FP32 y of the money's sign
         // (|y| >= 2^-48) and 0 otherwise, so y I is the in-place value and I
-        // the count (multiplies instead of compares and selects); paths at
-        // or beyond nloc (last CTA) take 0 by selects
+        // the count (multiplies instead of compares and selects).  Path
+        // pairs: y I, y^2 and y^3 in packed f32x2, the moments summed path
+        // by path in FP32 (the same sums as one path at a time); paths at or
+        // beyond nloc (last CTA) take 0 by selects
         float g[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) g[k] = 0.f;
         E *sl = sm.S[d % kSlots];
         const float big = PUT ? -0x1p100f : 0x1p100f;
-        auto one = [&](float yr, bool valid, float &yo) {
-            const float in = valid ? __saturatef(yr * big) : 0.f;
-            const float y = valid ? yr * in : 0.f;
-            yo = y;
-            const float yy = y * y, y3 = yy * y;
-            g[0] += in;
-            g[1] += y;
-            g[2] += yy;
-            g[3] += y3;
-            g[4] = fmaf(yy, yy, g[4]);
-            g[5] = fmaf(yy, y3, g[5]);
-            g[6] = fmaf(y3, y3, g[6]);
+        auto pair = [&](int idx, bool tail) {
+            const f2 Yr = raw_y2(sl, idx, invK);
+            float in[2] = {__saturatef(f2_lo(Yr) * big), __saturatef(f2_hi(Yr) * big)};
+            f2 Y;
+            if (tail) {
+                const bool v0 = idx < nloc, v1 = idx + 1 < nloc;
+                in[0] = v0 ? in[0] : 0.f;
+                in[1] = v1 ? in[1] : 0.f;
+                Y = f2_pack(v0 ? f2_lo(Yr) * in[0] : 0.f, v1 ? f2_hi(Yr) * in[1] : 0.f);
+            } else {
+                Y = f2_mul(Yr, f2_pack(in[0], in[1]));
+            }
+            put_y2(sl, idx, Y);
+            const f2 YY = f2_mul(Y, Y), Y3 = f2_mul(YY, Y);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float y = h ? f2_hi(Y) : f2_lo(Y), yy = h ? f2_hi(YY) : f2_lo(YY), y3 = h ? f2_hi(Y3) : f2_lo(Y3);
+                g[0] += in[h];
+                g[1] += y;
+                g[2] += yy;
+                g[3] += y3;
+                g[4] = fmaf(yy, yy, g[4]);
+                g[5] = fmaf(yy, y3, g[5]);
+                g[6] = fmaf(y3, y3, g[6]);
+            }
         };
 #pragma unroll
-        for (int i = 0; i < kPPT; i += 2) {
-            const int idx = pidx(i);
-            const f2 yr = raw_y2(sl, idx, invK);
-            float ylo, yhi;
-            one(f2_lo(yr), idx < nloc, ylo);
-            one(f2_hi(yr), idx + 1 < nloc, yhi);
-            put_y2(sl, idx, f2_pack(ylo, yhi));
-        }
+        for (int i = 0; i < kPPT; i += 2) pair(pidx(i), nloc < kPPC);
         fence_proxy_async();             // these generic writes precede a later TMA refill
         const float r = warp_sum8(g, lane);
         const int k = (lane >> 2) & 7;
@@ -398,19 +406,18 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
             }
             return;
         }
+        // with y in place (0 off the money), "in the money and h > c(y)" is
+        // h > max(c(y), 0), h = -y (put) or y (call)
         const f2 B0 = f2_splat(b0), B1 = f2_splat(b1), B2 = f2_splat(b2), B3 = f2_splat(b3);
+        const f2 SG = f2_splat(PUT ? -1.f : 1.f);
 #pragma unroll
         for (int i = 0; i < kPPT; i += 2) {
             const f2 Y = y2_at(sl, pidx(i));
             const f2 C = f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0);
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const float y = h2 ? f2_hi(Y) : f2_lo(Y);
-                const float cont = h2 ? f2_hi(C) : f2_lo(C);
-                const float h = PUT ? -y : y;
-                const bool ex = (PUT ? y < 0.f : y > 0.f) && h > cont;
-                cf[i + h2] = ex ? h : cf[i + h2];
-            }
+            const f2 H = f2_mul(Y, SG);
+            const float hl = f2_lo(H), hh = f2_hi(H);
+            cf[i] = hl > fmaxf(f2_lo(C), 0.f) ? hl : cf[i];
+            cf[i + 1] = hh > fmaxf(f2_hi(C), 0.f) ? hh : cf[i + 1];
         }
     };
 
@@ -456,7 +463,8 @@ __global__ void __launch_bounds__(kT, 1) sweep_lsm_v2_kernel(const __grid_consta
                     const f2 C = f2_mul(f2_pack(cf[i], cf[i + 1]), DISC);
                     cf[i] = f2_lo(C);
                     cf[i + 1] = f2_hi(C);
-                    R0 = f2_add(R0, f2_pack(f2_lo(Y) != 0.f ? cf[i] : 0.f, f2_hi(Y) != 0.f ? cf[i + 1] : 0.f));
+                    const float big = PUT ? -0x1p100f : 0x1p100f;          // in-the-money indicator, as in the Gram pass
+                    R0 = f2_fma(C, f2_pack(__saturatef(f2_lo(Y) * big), __saturatef(f2_hi(Y) * big)), R0);
                     const f2 YY = f2_mul(Y, Y);
                     R1 = f2_fma(C, Y, R1);                        // y = 0 off the money
                     R2 = f2_fma(C, YY, R2);
