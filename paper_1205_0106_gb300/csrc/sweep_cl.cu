@@ -561,12 +561,14 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                     const E *sr = sm.S[d % kSlots];
                     f2 R0 = z2, R1 = z2, R2 = z2, R3 = z2;
                     // P4: the cubic basis; otherwise b3 = 0 and R3 is not used (p <= 3)
-                    auto ex_rhs = [&](auto P4) {
+                    // EX: exercise at d+1 as well (a compile-time branch: each variant
+                    // is one straight run of the 8 pairs)
+                    auto ex_rhs = [&](auto P4, auto EX) {
                         constexpr bool Q4 = decltype(P4)::value;
 #pragma unroll
                     for (int i = 0; i < kPPT; i += 2) {
                         const int idx = pidx(i);
-                        if (ex) {
+                        if constexpr (decltype(EX)::value) {
                             const f2 Y = y2_at(se, idx);
                             const f2 C = Q4 ? f2_fma(f2_fma(f2_fma(B3, Y, B2), Y, B1), Y, B0)
                                             : f2_fma(f2_fma(B2, Y, B1), Y, B0);
@@ -587,7 +589,10 @@ __global__ void __launch_bounds__(kT, 1) sweep_cl_kernel(const __grid_constant__
                         if (Q4) R3 = f2_fma(C, f2_mul(YY, Y), R3);
                     }
                     };
-                    ex_rhs(Q);
+                    if (ex)
+                        ex_rhs(Q, std::true_type{});
+                    else
+                        ex_rhs(Q, std::false_type{});
                     float rr[4] = {f2_lo(R0) + f2_hi(R0), f2_lo(R1) + f2_hi(R1), f2_lo(R2) + f2_hi(R2),
                                    f2_lo(R3) + f2_hi(R3)};
                     if (has_x) {                                          // the shared-memory path
